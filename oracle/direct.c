@@ -1,0 +1,127 @@
+/*
+ * FP64 direct-sum oracle for the Gaussian-regularised Biot-Savart velocity and the
+ * vortex-stretching term of a periodic vortex-particle system.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline may load this library.  It shares no code, header or table with the GPU path.
+ *
+ * Definitions followed (the plain O(N^2) sum, no approximation):
+ *   - Eq. (biotsavart): u_i = sum_j gamma_j x grad(G g_sigma), G = 1/(4 pi r).  Written out,
+ *     u_i = sum_n sum_j' K(r) gamma_j x r with r = x_i - x_j - n L.
+ *   - Eq. (cutoff): q(rho) = erf(rho/sqrt 2) - sqrt(2/pi) rho exp(-rho^2/2), rho = |r|/sigma,
+ *     which equals sqrt(2/pi) * int_0^rho s^2 exp(-s^2/2) ds (the Gaussian's enclosed fraction).
+ *     K(r) = q(rho) / (4 pi |r|^3).
+ *   - Eq. (stretching), read as the classical (gamma_i . grad) u evaluated at x_i:
+ *     S_i = sum_n sum_j' [ K gamma_j x gamma_i + F (gamma_i . r)(gamma_j x r) ],
+ *     F = K'(|r|)/|r| = [ sqrt(2/pi) exp(-rho^2/2)/(sigma^3 |r|^2) - 3 q/|r|^5 ] / (4 pi).
+ *   - Periodic images (Section 4.1, "3^3 x 3^3 x 3^3 - 1" images): a cube of image boxes
+ *     n in {-K..K}^3 around the primary box; K = 1 is 27 boxes, K = 13 is 27^3 boxes.
+ *   - sum' skips the self pair (j = i, n = 0), which contributes exactly zero anyway.
+ *
+ * Optional output G (3x3 per target, row a, column k) is the velocity gradient
+ * du_a/dx_k = sum eps_abc gamma_jb (K delta_ck + F r_c r_k), used by the gradient oracle.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_PI 3.14159265358979323846
+
+/* q(rho): for rho < 0.5 the integral's power series (term k: (-1)^k rho^(2k+3)/(2^k k! (2k+3))),
+ * otherwise the closed form with erf. Both are the definition in Eq. (cutoff). */
+static double oracle_q(double rho)
+{
+    const double c = sqrt(2.0 / ORACLE_PI);
+    if (rho < 0.5) {
+        double rho2 = rho * rho, pw = rho * rho2, fact = 1.0, sum = 0.0;
+        for (int k = 0; k < 30; ++k) {
+            double term = pw / (fact * (2.0 * k + 3.0));
+            sum += (k & 1) ? -term : term;
+            if (term < 1e-20 * fabs(sum)) break;
+            pw *= rho2;
+            fact *= 2.0 * (k + 1);
+        }
+        return c * sum;
+    }
+    return erf(rho / sqrt(2.0)) - c * rho * exp(-0.5 * rho * rho);
+}
+
+double oracle_cutoff_q(double rho) { return oracle_q(rho); }
+
+/* Levi-Civita symbol eps_abc. */
+static inline int levi_civita(int a, int b, int c)
+{
+    return ((a - b) * (b - c) * (c - a)) / 2;
+}
+
+/* Add the contribution of one source (position already shifted by its image) to a target. */
+static inline void pair(const double xt[3], const double gt[3], const double xs[3], const double gs[3],
+                        double sigma, double u[3], double S[3], double G[9])
+{
+    double r[3] = {xt[0] - xs[0], xt[1] - xs[1], xt[2] - xs[2]};
+    double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    if (r2 == 0.0) return;
+    double rr = sqrt(r2);
+    double rho = rr / sigma;
+    double q = oracle_q(rho);
+    double K = q / (4.0 * ORACLE_PI * rr * r2);
+    double F = (sqrt(2.0 / ORACLE_PI) * exp(-0.5 * rho * rho) / (sigma * sigma * sigma * r2)
+                - 3.0 * q / (r2 * r2 * rr)) / (4.0 * ORACLE_PI);
+    double W[3] = {gs[1] * r[2] - gs[2] * r[1], gs[2] * r[0] - gs[0] * r[2], gs[0] * r[1] - gs[1] * r[0]};
+    double X[3] = {gs[1] * gt[2] - gs[2] * gt[1], gs[2] * gt[0] - gs[0] * gt[2], gs[0] * gt[1] - gs[1] * gt[0]};
+    double gr = gt[0] * r[0] + gt[1] * r[1] + gt[2] * r[2];
+    for (int a = 0; a < 3; ++a) {
+        u[a] += K * W[a];
+        S[a] += K * X[a] + F * gr * W[a];
+    }
+    if (G) {
+        /* du_a/dx_k = eps_abc gs_b (K delta_ck + F r_c r_k) = K eps_abk gs_b + F W_a r_k */
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 3; ++k) {
+                double epsterm = 0.0;
+                for (int b = 0; b < 3; ++b) epsterm += levi_civita(a, b, k) * gs[b];
+                G[3 * a + k] += K * epsterm + F * W[a] * r[k];
+            }
+    }
+}
+
+/*
+ * Direct sum at nt targets from ns sources with image boxes n, kmin <= max|n_i| <= kmax.
+ * xs, gs: ns x 3 source positions and strengths.  xt, gt: nt x 3 target positions and the
+ * target strengths used by the stretching term.  tidx[i] is the source index of target i
+ * (excluded at n = 0) or -1.  u, S: nt x 3 outputs (overwritten).  G: nt x 9 or NULL.
+ * nthreads <= 0 uses the OpenMP default.
+ */
+void oracle_direct(int64_t ns, const double *xs, const double *gs,
+                   int64_t nt, const double *xt, const double *gt, const int64_t *tidx,
+                   double sigma, double L, int kmin, int kmax,
+                   double *u, double *S, double *G, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    (void)nthreads;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < nt; ++i) {
+        double ui[3] = {0, 0, 0}, Si[3] = {0, 0, 0}, Gi[9] = {0};
+        const double *x0 = xt + 3 * i, *g0 = gt + 3 * i;
+        for (int nx = -kmax; nx <= kmax; ++nx)
+            for (int ny = -kmax; ny <= kmax; ++ny)
+                for (int nz = -kmax; nz <= kmax; ++nz) {
+                    int m = abs(nx); if (abs(ny) > m) m = abs(ny); if (abs(nz) > m) m = abs(nz);
+                    if (m < kmin) continue;
+                    int primary = (nx == 0 && ny == 0 && nz == 0);
+                    for (int64_t j = 0; j < ns; ++j) {
+                        if (primary && tidx && tidx[i] == j) continue;
+                        double xsj[3] = {xs[3 * j] + nx * L, xs[3 * j + 1] + ny * L, xs[3 * j + 2] + nz * L};
+                        pair(x0, g0, xsj, gs + 3 * j, sigma, ui, Si, G ? Gi : NULL);
+                    }
+                }
+        for (int a = 0; a < 3; ++a) { u[3 * i + a] = ui[a]; S[3 * i + a] = Si[a]; }
+        if (G) for (int a = 0; a < 9; ++a) G[9 * i + a] = Gi[a];
+    }
+}

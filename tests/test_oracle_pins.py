@@ -1,0 +1,250 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test targets one plausible mistake: a wrong normalisation of q (Eq. cutoff), a
+wrong sign or operand order in the cross products (Eq. biotsavart), a dropped or
+mis-signed term in F (Eq. stretching), a wrong image lattice (Section 4.1).
+"""
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.special import erf
+
+import oracle
+import workload as wl
+
+FOUR_PI = 4.0 * np.pi
+
+
+def test_q_matches_enclosed_gaussian_fraction():
+    # q(rho) is the fraction of a 3-D Gaussian inside radius rho (Eq. cutoff derivation)
+    for rho in [1e-3, 0.05, 0.3, 0.4999, 0.5, 0.5001, 1.0, 2.0, 3.7, 6.0, 8.0]:
+        val, _ = integrate.quad(lambda s: s * s * np.exp(-0.5 * s * s), 0.0, rho,
+                                epsabs=0, epsrel=1e-13, limit=200)
+        ref = np.sqrt(2.0 / np.pi) * val
+        assert abs(oracle.cutoff_q(rho) - ref) <= 2e-13 * ref + 1e-17, rho
+
+
+def test_q_limits():
+    assert oracle.cutoff_q(9.0) == 1.0          # 1 - q(9) < half an ulp of 1
+    assert abs(oracle.cutoff_q(8.0) - 1.0) < 1e-13
+    rho = 1e-4                                   # leading term sqrt(2/pi) rho^3 / 3
+    assert abs(oracle.cutoff_q(rho) / (np.sqrt(2 / np.pi) * rho ** 3 / 3) - 1) < 1e-8
+
+
+def _blob_psi(x, gamma, sigma):
+    """Stream function of one Gaussian vortex blob at the origin: gamma erf(r/(sqrt2 s))/(4 pi r)."""
+    r = np.linalg.norm(x)
+    return gamma * erf(r / (np.sqrt(2) * sigma)) / (FOUR_PI * r)
+
+
+def _curl_fd(f, x, eps):
+    J = np.zeros((3, 3))   # J[c, k] = d f_c / d x_k
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = eps
+        J[:, k] = (f(x + e) - f(x - e)) / (2 * eps)
+    return np.array([J[2, 1] - J[1, 2], J[0, 2] - J[2, 0], J[1, 0] - J[0, 1]])
+
+
+@pytest.mark.parametrize("sigma", [0.3, 1.0])
+def test_single_blob_closed_form(sigma):
+    # velocity of a single Gaussian blob = curl of its closed-form stream function
+    rng = np.random.default_rng(11)
+    g0 = np.array([0.3, -1.1, 0.7])
+    src = np.zeros((1, 3))
+    pts = rng.normal(size=(12, 3)) * sigma * np.array([[0.2], [0.5], [1], [1.5], [2], [3],
+                                                       [4], [6], [0.8], [1.2], [2.5], [5]])
+    u, _ = oracle.direct(src, g0[None], sigma, K=0, xt=pts)
+    for i, x in enumerate(pts):
+        ref = _curl_fd(lambda y: _blob_psi(y, g0, sigma), x, 1e-5 * sigma)
+        assert np.allclose(u[i], ref, rtol=1e-7, atol=1e-9 * np.abs(ref).max()), (i, u[i], ref)
+
+
+def test_singular_far_limit_and_laplace_identity():
+    # for rho >= 9 every q is exactly 1: u is the textbook singular Biot-Savart sum and
+    # equals the curl of the Laplace vector potential sum gamma_j/(4 pi r)
+    rng = np.random.default_rng(5)
+    xs = rng.uniform(0, 1, (20, 3))
+    gs = rng.normal(size=(20, 3))
+    xt = rng.uniform(0, 1, (7, 3)) + np.array([3.0, 0, 0])
+    sigma = 0.2   # min distance > 2 -> rho > 10
+    u, S = oracle.direct(xs, gs, sigma, K=0, xt=xt, gt=np.ones_like(xt))
+    for i in range(len(xt)):
+        psi = lambda y: (gs / (FOUR_PI * np.linalg.norm(y - xs, axis=1))[:, None]).sum(0)
+        ref = _curl_fd(psi, xt[i], 1e-5)
+        assert np.allclose(u[i], ref, rtol=1e-8), (u[i], ref)
+
+
+def _mp_sum(xs, gs, xt, gt, tidx, sigma, L, K):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    out_u, out_S = [], []
+    s = mp.mpf(sigma)
+    for i in range(len(xt)):
+        u = [mp.mpf(0)] * 3
+        S = [mp.mpf(0)] * 3
+        xi = [mp.mpf(v) for v in xt[i]]
+        gi = [mp.mpf(v) for v in gt[i]]
+        for nx in range(-K, K + 1):
+            for ny in range(-K, K + 1):
+                for nz in range(-K, K + 1):
+                    for j in range(len(xs)):
+                        if nx == ny == nz == 0 and tidx[i] == j:
+                            continue
+                        r = [xi[0] - mp.mpf(xs[j][0]) - nx * mp.mpf(L),
+                             xi[1] - mp.mpf(xs[j][1]) - ny * mp.mpf(L),
+                             xi[2] - mp.mpf(xs[j][2]) - nz * mp.mpf(L)]
+                        r2 = r[0] ** 2 + r[1] ** 2 + r[2] ** 2
+                        rr = mp.sqrt(r2)
+                        rho = rr / s
+                        # q as the integral of the Gaussian shell density
+                        q = mp.sqrt(2 / mp.pi) * mp.quad(lambda t: t * t * mp.exp(-t * t / 2), [0, rho])
+                        Kk = q / (4 * mp.pi * rr ** 3)
+                        # F = K'(r)/r by mpmath differentiation of K(r)
+                        Kf = lambda R: (mp.sqrt(2 / mp.pi) * mp.quad(lambda t: t * t * mp.exp(-t * t / 2),
+                                                                     [0, R / s])) / (4 * mp.pi * R ** 3)
+                        F = mp.diff(Kf, rr) / rr
+                        g = [mp.mpf(v) for v in gs[j]]
+                        W = [g[1] * r[2] - g[2] * r[1], g[2] * r[0] - g[0] * r[2], g[0] * r[1] - g[1] * r[0]]
+                        X = [g[1] * gi[2] - g[2] * gi[1], g[2] * gi[0] - g[0] * gi[2], g[0] * gi[1] - g[1] * gi[0]]
+                        gr = gi[0] * r[0] + gi[1] * r[1] + gi[2] * r[2]
+                        for a in range(3):
+                            u[a] += Kk * W[a]
+                            S[a] += Kk * X[a] + F * gr * W[a]
+        out_u.append([float(v) for v in u])
+        out_S.append([float(v) for v in S])
+    return np.array(out_u), np.array(out_S)
+
+
+@pytest.mark.slow
+def test_bruteforce_mpmath_small():
+    # N = 8 jittered lattice with one image layer, three targets, 40-digit arithmetic;
+    # q and F come from numerical integration/differentiation, not from the erf formula
+    L = 2 * np.pi
+    n = 2
+    h = L / n
+    x = wl.jitter(wl.lattice_positions(n), h, 0.3, seed=4)
+    g = np.random.default_rng(8).normal(size=x.shape)
+    sigma = 0.8 * h
+    tid = np.array([0, 3, 6])
+    u, S = oracle.direct(x, g, sigma, K=1, targets=tid)
+    um, Sm = _mp_sum(x, g, x[tid], g[tid], tid, sigma, L, 1)
+    assert np.allclose(u, um, rtol=1e-12, atol=1e-14 * np.abs(um).max())
+    assert np.allclose(S, Sm, rtol=1e-11, atol=1e-13 * np.abs(Sm).max())
+
+
+def test_stretching_equals_directional_derivative_of_u():
+    # S_i = (gamma_i . grad) u at x_i, checked by central differences of the oracle's own u;
+    # the displaced point lies on the line through x_i along gamma_i, where the self blob's
+    # velocity gamma_i x d vanishes, so the self term needs no special handling.
+    f = wl.make_vortex_lattice(6, 2, 7)
+    x, g, s = f["x"], f["alpha"], f["sigma"]
+    tid = np.array([0, 17, 100, 215])
+    u, S = oracle.direct(x, g, s, K=1, targets=tid)
+    eps = 1e-4 * f["h"]
+    for k, i in enumerate(tid):
+        gi = g[i]
+        gh = gi / np.linalg.norm(gi)
+        up, _ = oracle.direct(x, g, s, K=1, xt=(x[i] + eps * gh)[None])
+        um, _ = oracle.direct(x, g, s, K=1, xt=(x[i] - eps * gh)[None])
+        fd = (up[0] - um[0]) / (2 * eps) * np.linalg.norm(gi)
+        assert np.allclose(S[k], fd, rtol=1e-6, atol=1e-8 * np.abs(fd).max()), (S[k], fd)
+
+
+def test_gradient_tensor_matches_fd_and_invariants():
+    f = wl.make_vortex_lattice(6, 2, 9)
+    x, g, s = f["x"], f["alpha"], f["sigma"]
+    tid = np.arange(0, 216, 7)
+    u, S, G = oracle.direct(x, g, s, K=1, targets=tid, grad=True)
+    # S = G gamma_i
+    assert np.allclose(S, np.einsum("iak,ik->ia", G, g[tid]), rtol=1e-12, atol=1e-15)
+    # divergence-free
+    assert np.abs(np.trace(G, axis1=1, axis2=2)).max() < 1e-12 * np.abs(G).max()
+    eps = 1e-4 * f["h"]
+    for k, i in enumerate(tid[:5]):
+        J = np.zeros((3, 3))
+        for d in range(3):
+            e = np.zeros(3)
+            e[d] = eps
+            # offset along an axis: the self blob contributes gamma_i x e K(eps), equal and
+            # opposite at +-e, so remove it by excluding the source i explicitly
+            mask = np.ones(len(x), bool)
+            mask[i] = False
+            up, _ = oracle.direct(x[mask], g[mask], s, K=1, xt=(x[i] + e)[None])
+            um, _ = oracle.direct(x[mask], g[mask], s, K=1, xt=(x[i] - e)[None])
+            # add back the images of particle i itself (n != 0)
+            ui_p, _ = oracle.direct(x[i:i + 1], g[i:i + 1], s, K=1, kmin=1, xt=(x[i] + e)[None])
+            ui_m, _ = oracle.direct(x[i:i + 1], g[i:i + 1], s, K=1, kmin=1, xt=(x[i] - e)[None])
+            J[:, d] = ((up + ui_p) - (um + ui_m))[0] / (2 * eps)
+        assert np.allclose(G[k], J, rtol=1e-6, atol=1e-8 * np.abs(J).max()), (G[k], J)
+
+
+def test_transpose_scheme_conserves_total_vorticity():
+    # sum_i (grad u_i)^T gamma_i = 0 exactly: each pair's two terms cancel
+    f = wl.make_vortex_lattice(6, 2, 3)
+    x, g, s = f["x"], f["alpha"], f["sigma"]
+    _, _, G = oracle.direct(x, g, s, K=1, grad=True)
+    tot = np.einsum("iak,ia->k", G, g)
+    scale = np.abs(np.einsum("iak,ia->ik", G, g)).sum()
+    assert np.abs(tot).max() < 1e-13 * scale
+
+
+def test_pair_antisymmetry_linearity_symmetry():
+    rng = np.random.default_rng(2)
+    # two particles with equal strength: equal and opposite velocities (no images)
+    x = np.array([[0.1, 0.2, 0.3], [0.5, -0.1, 0.2]])
+    gsame = np.array([[0.3, 0.4, -0.2]] * 2)
+    u, _ = oracle.direct(x, gsame, 0.3, K=0)
+    assert np.allclose(u[0], -u[1], rtol=1e-14, atol=1e-16)
+    # linearity and the symmetry <w, A gamma> = <A w, gamma> of the Biot-Savart matrix
+    f = wl.make_vortex_lattice(5, 2, 1)
+    x, s = f["x"], f["sigma"]
+    a = rng.normal(size=x.shape)
+    b = rng.normal(size=x.shape)
+    ua, _ = oracle.direct(x, a, s, K=1)
+    ub, _ = oracle.direct(x, b, s, K=1)
+    uab, _ = oracle.direct(x, 2.0 * a - 3.0 * b, s, K=1)
+    assert np.allclose(uab, 2.0 * ua - 3.0 * ub, rtol=1e-12, atol=1e-13 * np.abs(uab).max())
+    lhs = np.sum(b * ua)
+    rhs = np.sum(ub * a)
+    assert abs(lhs - rhs) < 1e-12 * (np.abs(b * ua).sum())
+
+
+def test_translation_invariance_of_full_lattice():
+    # moving every particle (and so every image) by d leaves u and S unchanged
+    f = wl.make_vortex_lattice(5, 2, 6)
+    x, g, s = f["x"], f["alpha"], f["sigma"]
+    tid = np.arange(0, 125, 9)
+    u0, S0 = oracle.direct(x, g, s, K=1, targets=tid)
+    u1, S1 = oracle.direct(x + np.array([0.3, -1.7, 2.2]), g, s, K=1, targets=tid)
+    assert np.allclose(u0, u1, rtol=1e-10, atol=1e-12 * np.abs(u0).max())
+    assert np.allclose(S0, S1, rtol=1e-10, atol=1e-12 * np.abs(S0).max())
+
+
+def test_spectral_series_two_ways():
+    # FFT-folded lattice series and the direct mode sum agree (independent evaluations)
+    f = wl.make_vortex_lattice(8, 2, 1)
+    us, Ss = oracle.spectral.direct_series(f["x"], f["alpha"], f["sigma"])
+    ul, Sl = oracle.spectral.lattice(8, f["alpha"], f["sigma"])
+    assert np.abs(us - ul).max() < 1e-12 * np.abs(ul).max()
+    assert np.abs(Ss - Sl).max() < 1e-12 * np.abs(Sl).max()
+
+
+def test_image_cube_converges_to_periodic_series():
+    # the cube-of-images sum minus its uniform offset tends to the Fourier series,
+    # and S tends to it with no offset (Section 4.1 periodic images)
+    f = wl.make_vortex_lattice(8, 2, 1)
+    x, g, s = f["x"], f["alpha"], f["sigma"]
+    ul, Sl = oracle.spectral.lattice(8, g, s)
+    errs_u, errs_S = [], []
+    for K in (1, 2, 4):
+        u, S = oracle.direct(x, g, s, K=K)
+        d = u - ul
+        d -= d.mean(0)
+        errs_u.append(np.linalg.norm(d) / np.linalg.norm(ul))
+        errs_S.append(np.linalg.norm(S - Sl) / np.linalg.norm(Sl))
+    assert errs_u[0] > errs_u[1] > errs_u[2]
+    assert errs_S[0] > errs_S[1] > errs_S[2]
+    # the tail decays at least like 1/K^1.5
+    assert errs_u[2] < errs_u[0] / 4 ** 1.5
+    assert errs_S[2] < errs_S[0] / 4 ** 1.5
