@@ -16,7 +16,9 @@
  *     F = K'(|r|)/|r| = [ sqrt(2/pi) exp(-rho^2/2)/(sigma^3 |r|^2) - 3 q/|r|^5 ] / (4 pi).
  *   - Periodic images (Section 4.1, "3^3 x 3^3 x 3^3 - 1" images): a cube of image boxes
  *     n in {-K..K}^3 around the primary box; K = 1 is 27 boxes, K = 13 is 27^3 boxes.
- *   - sum' skips the self pair (j = i, n = 0), which contributes exactly zero anyway.
+ *   - sum' skips the self pair (j = i, n = 0), which contributes exactly zero anyway.  Any
+ *     other pair at r = 0 (coincident distinct particles) takes the finite r -> 0 limit of
+ *     the smoothed kernel: K(0) = sqrt(2/pi)/(12 pi sigma^3), F(0) = -sqrt(2/pi)/(20 pi sigma^5).
  *
  * Optional output G (3x3 per target, row a, column k) is the velocity gradient
  * du_a/dx_k = sum eps_abc gamma_jb (K delta_ck + F r_c r_k), used by the gradient oracle.
@@ -64,13 +66,31 @@ static inline void pair(const double xt[3], const double gt[3], const double xs[
 {
     double r[3] = {xt[0] - xs[0], xt[1] - xs[1], xt[2] - xs[2]};
     double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-    if (r2 == 0.0) return;
     double rr = sqrt(r2);
     double rho = rr / sigma;
-    double q = oracle_q(rho);
-    double K = q / (4.0 * ORACLE_PI * rr * r2);
-    double F = (sqrt(2.0 / ORACLE_PI) * exp(-0.5 * rho * rho) / (sigma * sigma * sigma * r2)
-                - 3.0 * q / (r2 * r2 * rr)) / (4.0 * ORACLE_PI);
+    double K, F;
+    if (rho < 0.5) {
+        /* K = k(rho)/(4 pi sigma^3), F = f(rho)/(4 pi sigma^5) with k = q/rho^3 and
+         * f = k'(rho)/rho from the same integral series; finite at r = 0 (the smoothed
+         * kernel of two coincident distinct particles). */
+        double x = rho * rho, xp = 1.0, xm1 = 1.0, fact = 1.0, k = 0.0, f = 0.0;
+        for (int q = 0; q < 30; ++q) {
+            double den = fact * (2.0 * q + 3.0);
+            k += (q & 1) ? -xp / den : xp / den;
+            if (q >= 1) f += (q & 1) ? -2.0 * q * xm1 / den : 2.0 * q * xm1 / den;
+            xm1 = xp;
+            xp *= x;
+            fact *= 2.0 * (q + 1);
+        }
+        double c = sqrt(2.0 / ORACLE_PI);
+        K = c * k / (4.0 * ORACLE_PI * sigma * sigma * sigma);
+        F = c * f / (4.0 * ORACLE_PI * sigma * sigma * sigma * sigma * sigma);
+    } else {
+        double q = oracle_q(rho);
+        K = q / (4.0 * ORACLE_PI * rr * r2);
+        F = (sqrt(2.0 / ORACLE_PI) * exp(-0.5 * rho * rho) / (sigma * sigma * sigma * r2)
+             - 3.0 * q / (r2 * r2 * rr)) / (4.0 * ORACLE_PI);
+    }
     double W[3] = {gs[1] * r[2] - gs[2] * r[1], gs[2] * r[0] - gs[0] * r[2], gs[0] * r[1] - gs[1] * r[0]};
     double X[3] = {gs[1] * gt[2] - gs[2] * gt[1], gs[2] * gt[0] - gs[0] * gt[2], gs[0] * gt[1] - gs[1] * gt[0]};
     double gr = gt[0] * r[0] + gt[1] * r[1] + gt[2] * r[2];

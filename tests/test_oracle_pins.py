@@ -248,3 +248,19 @@ def test_image_cube_converges_to_periodic_series():
     # the tail decays at least like 1/K^1.5
     assert errs_u[2] < errs_u[0] / 4 ** 1.5
     assert errs_S[2] < errs_S[0] / 4 ** 1.5
+
+
+def test_coincident_distinct_particles_take_the_smooth_limit():
+    # two different particles at one point: the smoothed kernel is finite there,
+    # K(0) = lim q/(4 pi r^3) = sqrt(2/pi)/(12 pi sigma^3), so S_1 = K(0) gamma_2 x gamma_1
+    sigma = 0.37
+    x = np.array([[1.0, 2.0, 3.0], [1.0, 2.0, 3.0]])
+    g = np.array([[0.3, -0.2, 0.5], [-0.4, 0.9, 0.1]])
+    u, S = oracle.direct(x, g, sigma, K=0)
+    K0 = np.sqrt(2 / np.pi) / (12 * np.pi * sigma ** 3)
+    assert np.allclose(u, 0.0, atol=1e-15)
+    assert np.allclose(S[0], K0 * np.cross(g[1], g[0]), rtol=1e-13)
+    # continuous with a tiny separation along gamma_1 (where the F term vanishes)
+    d = 1e-7 * sigma * g[0] / np.linalg.norm(g[0])
+    u2, S2 = oracle.direct(x[1:], g[1:], sigma, K=0, xt=(x[0] + d)[None], gt=g[:1])
+    assert np.allclose(S2[0], S[0], rtol=1e-9)
