@@ -1,0 +1,146 @@
+/*
+ * vfmm — periodic FMM evaluation of the Gaussian-regularised Biot-Savart velocity and
+ * vortex-stretching term of a vortex-particle system, for NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Yokota & Barba, "FMM-based vortex method for simulation of isotropic
+ * turbulence on GPUs, compared with a spectral method"):
+ *
+ *   u_i  = sum_n sum_j' K(r) gamma_j x r                                    Eq. (biotsavart)
+ *   S_i  = sum_n sum_j' [ K(r) gamma_j x gamma_i + F(r)(gamma_i . r)(gamma_j x r) ]
+ *        = (gamma_i . grad) u at x_i                                          Eq. (stretching)
+ *   r = x_i - x_j - n L,  rho = |r|/sigma,
+ *   q(rho) = erf(rho/sqrt2) - sqrt(2/pi) rho exp(-rho^2/2)                    Eq. (cutoff)
+ *   K = q/(4 pi |r|^3),  F = K'(|r|)/|r|
+ *
+ * over the image boxes n of a cube of 3^(S+1) boxes per side around the primary box
+ * [0, L)^3 (S = periodic_levels; S = 2 is the 27^3 images of Section 4.1), skipping the
+ * self pair.  The FMM (Section 3.1, Eqs. fmm3dm, fmm3dl, biotsavartfmm1-2,
+ * stretchingfmm1-2) evaluates the far field from expansions of the vector potential
+ * psi = sum_j gamma_j G with g_sigma = 1, and the near field exactly; the images beyond
+ * the central 3^3 boxes come from the root multipole through a precomputed lattice
+ * operator (Section 3.1, last paragraph; Section 5.6).
+ *
+ * Conventions
+ *  - Every function returns an int status: VFMM_OK (0) or a negative VFMM_ERR_* code.
+ *    vfmm_strerror() names a code; vfmm_last_error() gives the detail of the last
+ *    failure on a handle.
+ *  - Pointer arguments of vfmm_build_tree / vfmm_eval_* are DEVICE pointers owned by the
+ *    caller, contiguous row-major n x 3 arrays of float (cfg.dtype = VFMM_F32) or
+ *    double (VFMM_F64).  Outputs are in the caller's particle order.
+ *    vfmm_eval_host takes HOST pointers and does the copies itself.
+ *  - The handle owns all workspace (tree, expansions, operators); it allocates device
+ *    memory in vfmm_create / vfmm_build_tree / the first evaluation of a size.
+ *  - Work is enqueued on cfg.stream (a cudaStream_t; NULL = legacy default stream).
+ *    vfmm_eval_* is asynchronous: device-side errors (e.g. a leaf overflow) are
+ *    reported by the next vfmm_sync().  vfmm_build_tree synchronises the stream once to
+ *    read the leaf occupancy check.
+ *  - Handles are not thread-safe; use one handle per host thread.
+ */
+#ifndef VFMM_H
+#define VFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VFMM_OK 0
+#define VFMM_ERR_ARG (-1)         /* invalid argument (n <= 0, p < 2, non-finite sigma ...) */
+#define VFMM_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define VFMM_ERR_OOM (-3)         /* device allocation failed */
+#define VFMM_ERR_NOT_BUILT (-4)   /* evaluation before vfmm_build_tree */
+#define VFMM_ERR_BOUNDS (-5)      /* a device-side bounds check fired */
+#define VFMM_ERR_TIMEOUT (-6)     /* a bounded device-side wait gave up */
+#define VFMM_ERR_UNSUPPORTED (-7) /* configuration outside what is implemented */
+
+/* element type of the caller's arrays, and the arithmetic of P2P and the expansions */
+#define VFMM_F32 0
+#define VFMM_F64 1
+
+/* arithmetic of the M2L translations (FP32 / FP64 on CUDA cores; TF32 or BF16 inputs on
+ * the tensor cores with FP32 accumulation and a three-product hi/lo split) */
+#define VFMM_M2L_FP32 0
+#define VFMM_M2L_FP64 1
+#define VFMM_M2L_TF32X3 2
+#define VFMM_M2L_BF16X3 3
+
+/* evaluation method */
+#define VFMM_METHOD_FMM 0    /* tree + expansions + near field */
+#define VFMM_METHOD_DIRECT 1 /* all pairs over the (2K+1)^3 image cube, K = direct_images */
+
+typedef struct vfmm_config {
+    int p;               /* expansion order: degrees 0..p, (p+1)^2 coefficients (Eq. fmm3dm); 2 <= p <= 16 */
+    int depth;           /* leaf depth D of the uniform octree; 0 = choose from ncrit */
+    int ncrit;           /* target mean particles per leaf when depth == 0 */
+    int near_rings;      /* R: near field = (2R+1)^3 leaves; 0 = smallest R with R w >= rho_cut sigma; R <= 2 */
+    double rho_cut;      /* far-field pairs must satisfy |r| >= rho_cut sigma (default 6) */
+    int periodic_levels; /* S: image cube of 3^(S+1) boxes per side; 0 = the 27 central boxes only */
+    double box;          /* L, the period (default 2 pi) */
+    int dtype;           /* VFMM_F32 | VFMM_F64 */
+    int m2l_prec;        /* VFMM_M2L_*; with dtype F64 only VFMM_M2L_FP64 is accepted */
+    int method;          /* VFMM_METHOD_FMM | VFMM_METHOD_DIRECT */
+    int direct_images;   /* K for VFMM_METHOD_DIRECT */
+    void *stream;        /* cudaStream_t */
+} vfmm_config;
+
+typedef struct vfmm_ctx *vfmm_handle;
+
+/* Fill *cfg with defaults: p=10, depth=0, ncrit=64, near_rings=0, rho_cut=6, S=2, L=2 pi,
+ * F32, M2L BF16X3, FMM, K=1, stream NULL. */
+int vfmm_config_default(vfmm_config *cfg);
+
+/* Create a handle; precomputes the FP64 translation and lattice operators on the host and
+ * uploads them.  *out receives the handle (NULL on failure). */
+int vfmm_create(const vfmm_config *cfg, vfmm_handle *out);
+
+/* Release the handle and all its device memory (synchronises its stream). */
+int vfmm_destroy(vfmm_handle h);
+
+/* Change the stream later calls enqueue on. */
+int vfmm_set_stream(vfmm_handle h, void *stream);
+
+/* Sort n particles into the uniform octree (Section 3.2; tree construction ran on the CPU in
+ * the paper, Section 2.2).  x: device n x 3 positions; positions are wrapped into [0, L)^3
+ * by x - L floor(x/L) (any finite value is accepted).  Keys are leaf indices, the sort is a
+ * counting sort with a per-leaf index sort, so the order is deterministic.
+ * Errors: n <= 0 -> VFMM_ERR_ARG; a leaf with more than 4096 particles -> VFMM_ERR_UNSUPPORTED. */
+int vfmm_build_tree(vfmm_handle h, int64_t n, const void *x);
+
+/* u and S at every particle for strengths gamma (device n x 3, caller order) and core
+ * size sigma (Eqs. biotsavart, stretching).  u_out: device n x 3; s_out: device n x 3 or
+ * NULL to skip the stretching term.  Errors: sigma not finite or <= 0 -> VFMM_ERR_ARG;
+ * before vfmm_build_tree -> VFMM_ERR_NOT_BUILT; a near field that would need R > 2 ->
+ * VFMM_ERR_UNSUPPORTED (use a shallower tree). */
+int vfmm_eval_velocity_stretching(vfmm_handle h, const void *gamma, double sigma, void *u_out,
+                                  void *s_out);
+
+/* End to end from HOST memory: copies x and gamma to the device, builds the tree,
+ * evaluates, copies u and S back, and synchronises.  Pointers are host n x 3 arrays of the
+ * configured dtype; s_out may be NULL. */
+int vfmm_eval_host(vfmm_handle h, int64_t n, const void *x, const void *gamma, double sigma,
+                   void *u_out, void *s_out);
+
+/* Wait for the handle's stream; returns the first device-side error since the last call. */
+int vfmm_sync(vfmm_handle h);
+
+/* Milliseconds per phase of the last evaluation (CUDA events; valid after vfmm_sync):
+ * [0] tree build, [1] P2M, [2] M2M, [3] M2L, [4] periodic lattice operator, [5] L2L,
+ * [6] L2P, [7] P2P + output.  Writes min(nphase, 8) values. */
+int vfmm_get_timings(vfmm_handle h, double *ms_per_phase, int nphase);
+
+/* Tree facts: out[0] = depth D, out[1] = near rings R used by the last evaluation,
+ * out[2] = leaves per side, out[3] = maximum particles in one leaf, out[4] = particles. */
+int vfmm_get_tree_info(vfmm_handle h, int64_t *out, int nout);
+
+/* Name of a status code (static string). */
+const char *vfmm_strerror(int status);
+
+/* Detail message of the last failure on h (valid until the next call on h). */
+const char *vfmm_last_error(vfmm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VFMM_H */

@@ -1,0 +1,113 @@
+"""GB300-native periodic FMM for the vortex-particle velocity and stretching term.
+
+Python face of libvfmm (C-ABI in include/vfmm.h).  PyTorch supplies device memory and
+streams; every step of the evaluation runs in the library's CUDA kernels.
+"""
+import math
+
+from . import _native
+from ._native import (VfmmError, vfmm_create, vfmm_destroy, vfmm_build_tree,  # noqa: F401
+                      vfmm_eval_velocity_stretching, vfmm_eval_host, vfmm_sync,
+                      vfmm_get_timings, vfmm_get_tree_info, vfmm_set_stream, config_default)
+
+PRECISIONS = {"fp32": _native.VFMM_M2L_FP32, "fp64": _native.VFMM_M2L_FP64,
+              "tf32x3": _native.VFMM_M2L_TF32X3, "bf16x3": _native.VFMM_M2L_BF16X3}
+PHASES = ["tree", "p2m", "m2m", "m2l", "periodic", "l2l", "l2p", "p2p"]
+
+
+def make_config(p=10, depth=0, ncrit=64, near_rings=0, rho_cut=6.0, periodic_levels=2,
+                box=2 * math.pi, dtype="f32", m2l="bf16x3", method="fmm", direct_images=1,
+                stream=None):
+    c = config_default()
+    c.p = p
+    c.depth = depth
+    c.ncrit = ncrit
+    c.near_rings = near_rings
+    c.rho_cut = rho_cut
+    c.periodic_levels = periodic_levels
+    c.box = box
+    c.dtype = _native.VFMM_F64 if dtype in ("f64", "float64") else _native.VFMM_F32
+    if c.dtype == _native.VFMM_F64:
+        m2l = "fp64"
+    c.m2l_prec = PRECISIONS[m2l]
+    c.method = _native.VFMM_METHOD_DIRECT if method == "direct" else _native.VFMM_METHOD_FMM
+    c.direct_images = direct_images
+    c.stream = stream
+    return c
+
+
+class VortexFMM:
+    """One handle of libvfmm bound to torch tensors on the current CUDA device."""
+
+    def __init__(self, **kw):
+        import torch
+        self.torch = torch
+        self.dtype = torch.float64 if kw.get("dtype", "f32") in ("f64", "float64") else torch.float32
+        stream = torch.cuda.current_stream().cuda_stream
+        self.cfg = make_config(stream=stream, **kw)
+        self.h = vfmm_create(self.cfg)
+        self.n = 0
+
+    def close(self):
+        if self.h:
+            vfmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, t):
+        torch = self.torch
+        if not (t.is_cuda and t.dtype == self.dtype and t.is_contiguous() and t.dim() == 2 and t.shape[1] == 3):
+            raise ValueError("expected a contiguous CUDA (n, 3) tensor of %s" % self.dtype)
+
+    def build_tree(self, x):
+        self._check(x)
+        vfmm_set_stream(self.h, self.torch.cuda.current_stream().cuda_stream)
+        vfmm_build_tree(self.h, x.shape[0], x.data_ptr())
+        self.n = x.shape[0]
+
+    def eval(self, gamma, sigma, stretching=True, out=None):
+        self._check(gamma)
+        if self.n and gamma.shape[0] != self.n:
+            raise ValueError("gamma has %d rows, the tree %d" % (gamma.shape[0], self.n))
+        torch = self.torch
+        if out is None:
+            u = torch.empty_like(gamma)
+            s = torch.empty_like(gamma) if stretching else None
+        else:
+            u, s = out
+        vfmm_set_stream(self.h, torch.cuda.current_stream().cuda_stream)
+        vfmm_eval_velocity_stretching(self.h, gamma.data_ptr(), sigma, u.data_ptr(),
+                                      s.data_ptr() if s is not None else 0)
+        return u, s
+
+    def __call__(self, x, gamma, sigma, stretching=True):
+        self.build_tree(x)
+        return self.eval(gamma, sigma, stretching)
+
+    def sync(self):
+        vfmm_sync(self.h)
+
+    def timings(self):
+        return dict(zip(PHASES, vfmm_get_timings(self.h)))
+
+    def tree_info(self):
+        return vfmm_get_tree_info(self.h)
+
+    def eval_host(self, x, gamma, sigma, u=None, s=None):
+        """x, gamma: host numpy (n, 3) arrays of the handle's dtype (pinned for speed)."""
+        import numpy as np
+        npdt = np.float64 if self.dtype == self.torch.float64 else np.float32
+        x = np.ascontiguousarray(x, dtype=npdt)
+        gamma = np.ascontiguousarray(gamma, dtype=npdt)
+        if u is None:
+            u = np.empty_like(gamma)
+        if s is None:
+            s = np.empty_like(gamma)
+        vfmm_eval_host(self.h, x.shape[0], x.ctypes.data, gamma.ctypes.data, sigma,
+                       u.ctypes.data, s.ctypes.data)
+        return u, s

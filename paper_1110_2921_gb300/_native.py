@@ -1,0 +1,142 @@
+"""ctypes binding of libvfmm (include/vfmm.h): argument marshalling only.
+
+The library must exist (built by ``paper_1110_2921_gb300.build``); there is no fallback
+implementation, and importing fails loudly if it is missing.
+"""
+import ctypes
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libvfmm.so")
+
+VFMM_OK = 0
+VFMM_ERR_ARG = -1
+VFMM_ERR_CUDA = -2
+VFMM_ERR_OOM = -3
+VFMM_ERR_NOT_BUILT = -4
+VFMM_ERR_BOUNDS = -5
+VFMM_ERR_TIMEOUT = -6
+VFMM_ERR_UNSUPPORTED = -7
+VFMM_F32 = 0
+VFMM_F64 = 1
+VFMM_M2L_FP32 = 0
+VFMM_M2L_FP64 = 1
+VFMM_M2L_TF32X3 = 2
+VFMM_M2L_BF16X3 = 3
+VFMM_METHOD_FMM = 0
+VFMM_METHOD_DIRECT = 1
+
+
+class vfmm_config(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("depth", ctypes.c_int), ("ncrit", ctypes.c_int),
+                ("near_rings", ctypes.c_int), ("rho_cut", ctypes.c_double),
+                ("periodic_levels", ctypes.c_int), ("box", ctypes.c_double),
+                ("dtype", ctypes.c_int), ("m2l_prec", ctypes.c_int), ("method", ctypes.c_int),
+                ("direct_images", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class VfmmError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__("%s failed: %s (%d)%s" % (where, strerror(status), status,
+                                                   (": " + detail) if detail else ""))
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libvfmm.so is not built (run paper_1110_2921_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        H = ctypes.c_void_p
+        V = ctypes.c_void_p
+        sig = {
+            "vfmm_config_default": ([ctypes.POINTER(vfmm_config)], ctypes.c_int),
+            "vfmm_create": ([ctypes.POINTER(vfmm_config), ctypes.POINTER(H)], ctypes.c_int),
+            "vfmm_destroy": ([H], ctypes.c_int),
+            "vfmm_set_stream": ([H, V], ctypes.c_int),
+            "vfmm_build_tree": ([H, ctypes.c_int64, V], ctypes.c_int),
+            "vfmm_eval_velocity_stretching": ([H, V, ctypes.c_double, V, V], ctypes.c_int),
+            "vfmm_eval_host": ([H, ctypes.c_int64, V, V, ctypes.c_double, V, V], ctypes.c_int),
+            "vfmm_sync": ([H], ctypes.c_int),
+            "vfmm_get_timings": ([H, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
+            "vfmm_get_tree_info": ([H, ctypes.POINTER(ctypes.c_int64), ctypes.c_int], ctypes.c_int),
+            "vfmm_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "vfmm_last_error": ([H], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def strerror(status):
+    return lib().vfmm_strerror(int(status)).decode()
+
+
+def check(status, where, handle=None):
+    if status != VFMM_OK:
+        detail = ""
+        if handle:
+            detail = lib().vfmm_last_error(handle).decode()
+        raise VfmmError(status, where, detail)
+
+
+def config_default():
+    c = vfmm_config()
+    check(lib().vfmm_config_default(ctypes.byref(c)), "vfmm_config_default")
+    return c
+
+
+def vfmm_create(cfg):
+    h = ctypes.c_void_p()
+    check(lib().vfmm_create(ctypes.byref(cfg), ctypes.byref(h)), "vfmm_create")
+    return h
+
+
+def vfmm_destroy(h):
+    check(lib().vfmm_destroy(h), "vfmm_destroy")
+
+
+def vfmm_set_stream(h, stream_ptr):
+    check(lib().vfmm_set_stream(h, ctypes.c_void_p(stream_ptr)), "vfmm_set_stream", h)
+
+
+def vfmm_build_tree(h, n, x_ptr):
+    check(lib().vfmm_build_tree(h, int(n), ctypes.c_void_p(x_ptr)), "vfmm_build_tree", h)
+
+
+def vfmm_eval_velocity_stretching(h, gamma_ptr, sigma, u_ptr, s_ptr):
+    check(lib().vfmm_eval_velocity_stretching(h, ctypes.c_void_p(gamma_ptr), float(sigma),
+                                              ctypes.c_void_p(u_ptr),
+                                              ctypes.c_void_p(s_ptr) if s_ptr else None),
+          "vfmm_eval_velocity_stretching", h)
+
+
+def vfmm_eval_host(h, n, x_ptr, gamma_ptr, sigma, u_ptr, s_ptr):
+    check(lib().vfmm_eval_host(h, int(n), ctypes.c_void_p(x_ptr), ctypes.c_void_p(gamma_ptr),
+                               float(sigma), ctypes.c_void_p(u_ptr),
+                               ctypes.c_void_p(s_ptr) if s_ptr else None), "vfmm_eval_host", h)
+
+
+def vfmm_sync(h):
+    check(lib().vfmm_sync(h), "vfmm_sync", h)
+
+
+def vfmm_get_timings(h):
+    buf = (ctypes.c_double * 8)()
+    check(lib().vfmm_get_timings(h, buf, 8), "vfmm_get_timings", h)
+    return list(buf)
+
+
+def vfmm_get_tree_info(h):
+    buf = (ctypes.c_int64 * 5)()
+    check(lib().vfmm_get_tree_info(h, buf, 5), "vfmm_get_tree_info", h)
+    return {"depth": buf[0], "near_rings": buf[1], "leaves_per_side": buf[2],
+            "max_leaf": buf[3], "n": buf[4]}

@@ -1,0 +1,525 @@
+// C-ABI of libvfmm: handle management, tree build and the evaluation pipeline
+// P2M -> M2M -> (FP64 root + periodic lattice operator) -> M2L -> L2L -> L2P -> P2P.
+#include "common.cuh"
+#include "vfmm_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+struct vfmm_ctx {
+    vfmm::Ctx c;
+};
+
+using namespace vfmm;
+
+namespace {
+
+int fail(Ctx *c, int code, const std::string &msg)
+{
+    if (c) c->last_error = msg;
+    return code;
+}
+
+int cuda_fail(Ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? VFMM_ERR_OOM : VFMM_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int ensure(Ctx *c, DevBuf &b, size_t bytes, const char *what)
+{
+    if (b.bytes >= bytes && b.p) return VFMM_OK;
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes > 0 ? bytes : 16);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return cuda_fail(c, e, what);
+    }
+    b.bytes = bytes;
+    return VFMM_OK;
+}
+
+void release(DevBuf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+template <typename T> std::vector<T> to_at(const std::vector<double> &A, int nc, int pc)
+{
+    // A is [nc out][nc in] row-major; AT is [pc in][OUT_ROWS out]
+    std::vector<T> AT((size_t)pc * OUT_ROWS, T(0));
+    for (int k = 0; k < nc; ++k)
+        for (int j = 0; j < nc; ++j) AT[(size_t)j * OUT_ROWS + k] = (T)A[(size_t)k * nc + j];
+    return AT;
+}
+
+inline int tindex(int tx, int ty, int tz) { return ((tx + 3) * 7 + (ty + 3)) * 7 + (tz + 3); }
+
+template <typename T> int upload_vec(Ctx *c, DevBuf &b, const std::vector<T> &v, const char *what)
+{
+    int st = ensure(c, b, v.size() * sizeof(T), what);
+    if (st) return st;
+    cudaError_t e = cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    return VFMM_OK;
+}
+
+template <typename T> int build_operators(Ctx *c)
+{
+    const int p = c->p, nc = c->nc, pc = c->pc;
+    // M2L: k-block offset t (source = target + t) uses the operator of d = target - source = -t
+    std::vector<T> m2l((size_t)NT * pc * OUT_ROWS, T(0));
+    for (int tx = -3; tx <= 3; ++tx)
+        for (int ty = -3; ty <= 3; ++ty)
+            for (int tz = -3; tz <= 3; ++tz) {
+                if (std::abs(tx) <= 1 && std::abs(ty) <= 1 && std::abs(tz) <= 1) continue;
+                double d[3] = {-(double)tx, -(double)ty, -(double)tz};
+                std::vector<T> at = to_at<T>(ops::m2l_hat(d, p), nc, pc);
+                std::copy(at.begin(), at.end(), m2l.begin() + (size_t)tindex(tx, ty, tz) * pc * OUT_ROWS);
+            }
+    std::vector<T> m2m((size_t)8 * pc * OUT_ROWS), l2l((size_t)8 * pc * OUT_ROWS);
+    std::vector<double> m2m64((size_t)8 * nc * nc);
+    for (int b = 0; b < 8; ++b) {
+        int bx = (b >> 2) & 1, by = (b >> 1) & 1, bz = b & 1;
+        double e1[3] = {(bx - 0.5) / 2.0, (by - 0.5) / 2.0, (bz - 0.5) / 2.0};
+        std::vector<double> A = ops::m2m_hat(e1, 2.0, p);
+        std::copy(A.begin(), A.end(), m2m64.begin() + (size_t)b * nc * nc);
+        std::vector<T> at = to_at<T>(A, nc, pc);
+        std::copy(at.begin(), at.end(), m2m.begin() + (size_t)b * pc * OUT_ROWS);
+        double e2[3] = {bx - 0.5, by - 0.5, bz - 0.5};
+        std::vector<T> at2 = to_at<T>(ops::l2l_hat(e2, p), nc, pc);
+        std::copy(at2.begin(), at2.end(), l2l.begin() + (size_t)b * pc * OUT_ROWS);
+    }
+    std::vector<double> lat = ops::lattice_operator(p, c->cfg.periodic_levels);
+    int st;
+    if ((st = upload_vec(c, c->at_m2l, m2l, "M2L operators"))) return st;
+    if ((st = upload_vec(c, c->at_m2m, m2m, "M2M operators"))) return st;
+    if ((st = upload_vec(c, c->at_l2l, l2l, "L2L operators"))) return st;
+    if ((st = upload_vec(c, c->m2m_f64, m2m64, "FP64 M2M operators"))) return st;
+    if ((st = upload_vec(c, c->lattice_f64, lat, "lattice operator"))) return st;
+    if ((st = ensure(c, c->root_m, 3 * nc * sizeof(double), "root multipole"))) return st;
+
+    // k-block lists
+    std::vector<int4> kb;
+    for (int R = 1; R <= 2; ++R)
+        for (int g = 0; g < 8; ++g) {
+            int gx = (g >> 2) & 1, gy = (g >> 1) & 1, gz = g & 1;
+            c->kb_m2l_off[R][g] = (int)kb.size();
+            // children of the parent's 27 neighbours, minus the target's own (2R+1)^3 near field
+            for (int Tx = -1; Tx <= 1; ++Tx)
+                for (int Ty = -1; Ty <= 1; ++Ty)
+                    for (int Tz = -1; Tz <= 1; ++Tz)
+                        for (int b = 0; b < 8; ++b) {
+                            int tx = 2 * Tx + ((b >> 2) & 1) - gx;
+                            int ty = 2 * Ty + ((b >> 1) & 1) - gy;
+                            int tz = 2 * Tz + (b & 1) - gz;
+                            if (std::abs(tx) <= R && std::abs(ty) <= R && std::abs(tz) <= R) continue;
+                            kb.push_back(make_int4(tindex(tx, ty, tz), tx, ty, tz));
+                        }
+            c->kb_m2l_cnt[R][g] = (int)kb.size() - c->kb_m2l_off[R][g];
+        }
+    c->kb_m2m_off = (int)kb.size();
+    for (int b = 0; b < 8; ++b) kb.push_back(make_int4(b, (b >> 2) & 1, (b >> 1) & 1, b & 1));
+    for (int g = 0; g < 8; ++g) {
+        c->kb_l2l_off[g] = (int)kb.size();
+        kb.push_back(make_int4(g, 0, 0, 0));
+    }
+    if ((st = upload_vec(c, c->kblocks, kb, "k-block lists"))) return st;
+    return VFMM_OK;
+}
+
+int check_device_error(Ctx *c)
+{
+    int e = 0;
+    cudaError_t ce = cudaMemcpyAsync(&e, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "device sync");
+    if (e) {
+        cudaMemsetAsync(c->err.p, 0, sizeof(int), c->stream);
+        if (e & ERRBIT_LEAF_OVERFLOW)
+            return fail(c, VFMM_ERR_UNSUPPORTED, "a leaf holds more particles than the per-leaf sort capacity (4096); use a deeper tree");
+        if (e & ERRBIT_TIMEOUT) return fail(c, VFMM_ERR_TIMEOUT, "a bounded device wait gave up");
+        return fail(c, VFMM_ERR_BOUNDS, "a device bounds check fired");
+    }
+    return VFMM_OK;
+}
+
+int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out)
+{
+    if (!c->built) return fail(c, VFMM_ERR_NOT_BUILT, "vfmm_build_tree has not been called");
+    if (!gamma || !u_out) return fail(c, VFMM_ERR_ARG, "null gamma or u_out");
+    if (!std::isfinite(sigma) || sigma <= 0.0) return fail(c, VFMM_ERR_ARG, "sigma must be finite and > 0");
+    const bool fmm = c->cfg.method == VFMM_METHOD_FMM;
+    int R;
+    if (fmm) {
+        R = c->cfg.near_rings;
+        if (R <= 0) {
+            R = 1;
+            while (R * c->leaf_w < c->cfg.rho_cut * sigma && R < 3) ++R;
+        }
+        if (R > 2)
+            return fail(c, VFMM_ERR_UNSUPPORTED,
+                        "the near field would need more than 2 rings of leaves (rho_cut * sigma > 2 * leaf width); use a shallower tree");
+    } else {
+        R = c->cfg.direct_images;
+    }
+    c->last_R = R;
+    cudaStream_t st = c->stream;
+    int rc;
+    cudaEventRecord(c->ev[2], st);
+    if ((rc = launch_gather_gamma(c, gamma))) return rc;
+    const void *uf = nullptr, *sf = nullptr;
+    if (fmm) {
+        const int D = c->depth;
+        const int S = c->cfg.periodic_levels;
+        const int4 *kbd = (const int4 *)c->kblocks.p;
+        char *M = (char *)c->mexp.p, *L = (char *)c->lexp.p;
+        auto lvl = [&](char *base, int l) { return (void *)(base + c->lvl_off[l] * c->esz); };
+        if ((rc = launch_p2m(c))) return rc;
+        cudaEventRecord(c->ev[3], st);
+        for (int l = D - 1; l >= 1; --l) {
+            GemmParams gp = {};
+            gp.AT = c->at_m2m.p;
+            gp.B = lvl(M, l + 1);
+            gp.C = lvl(M, l);
+            gp.kb = kbd;
+            gp.kb_off[0] = c->kb_m2m_off;
+            gp.kb_cnt[0] = 8;
+            gp.n_src = 1 << (l + 1);
+            gp.n_tgt = 1 << l;
+            gp.mode = 1;
+            gp.grouped = 0;
+            gp.accumulate = 0;
+            gp.pc = c->pc;
+            if ((rc = launch_gemm(c, gp, 1, (int64_t)1 << (3 * l)))) return rc;
+        }
+        cudaEventRecord(c->ev[4], st);
+        if (S > 0) {
+            if ((rc = launch_root(c))) return rc;
+        }
+        cudaEventRecord(c->ev[5], st);
+        const bool tc = c->cfg.m2l_prec == VFMM_M2L_TF32X3 || c->cfg.m2l_prec == VFMM_M2L_BF16X3;
+        for (int l = 1; l <= D; ++l) {
+            int Rl = (l == D) ? R : 1;
+            if (tc && l >= 3) {
+                bool bf = c->cfg.m2l_prec == VFMM_M2L_BF16X3;
+                if ((rc = launch_split(c, l, bf))) return rc;
+                if ((rc = launch_tc_m2l(c, l, kbd, c->kb_m2l_off[Rl], c->kb_m2l_cnt[Rl], bf))) return rc;
+                continue;
+            }
+            GemmParams gp = {};
+            gp.AT = c->at_m2l.p;
+            gp.B = lvl(M, l);
+            gp.C = lvl(L, l);
+            gp.kb = kbd;
+            for (int g = 0; g < 8; ++g) {
+                gp.kb_off[g] = c->kb_m2l_off[Rl][g];
+                gp.kb_cnt[g] = c->kb_m2l_cnt[Rl][g];
+            }
+            gp.n_src = gp.n_tgt = 1 << l;
+            gp.mode = 0;
+            gp.grouped = 1;
+            gp.accumulate = 0;
+            gp.pc = c->pc;
+            if ((rc = launch_gemm(c, gp, 8, (int64_t)1 << (3 * (l - 1))))) return rc;
+        }
+        cudaEventRecord(c->ev[6], st);
+        for (int l = 1; l <= D; ++l) {
+            if (l == 1 && S == 0) continue;
+            GemmParams gp = {};
+            gp.AT = c->at_l2l.p;
+            gp.B = lvl(L, l - 1);
+            gp.C = lvl(L, l);
+            gp.kb = kbd;
+            for (int g = 0; g < 8; ++g) {
+                gp.kb_off[g] = c->kb_l2l_off[g];
+                gp.kb_cnt[g] = 1;
+            }
+            gp.n_src = 1 << (l - 1);
+            gp.n_tgt = 1 << l;
+            gp.mode = 2;
+            gp.grouped = 1;
+            gp.accumulate = 1;
+            gp.pc = c->pc;
+            if ((rc = launch_gemm(c, gp, 8, (int64_t)1 << (3 * (l - 1))))) return rc;
+        }
+        cudaEventRecord(c->ev[7], st);
+        if ((rc = launch_l2p(c))) return rc;
+        uf = c->ufar.p;
+        sf = c->sfar.p;
+    } else {
+        for (int k = 3; k <= 7; ++k) cudaEventRecord(c->ev[k], st);
+    }
+    cudaEventRecord(c->ev[8], st);
+    if ((rc = launch_p2p(c, R, sigma, uf, sf, u_out, s_out, 0))) return rc;
+    cudaEventRecord(c->ev[9], st);
+    c->timed_eval = true;
+    return VFMM_OK;
+}
+
+int build_impl(Ctx *c, int64_t n, const void *x)
+{
+    if (n <= 0) return fail(c, VFMM_ERR_ARG, "n must be > 0");
+    if (n > (int64_t)1 << 30) return fail(c, VFMM_ERR_UNSUPPORTED, "n above 2^30 particles");
+    if (!x) return fail(c, VFMM_ERR_ARG, "null x");
+    int D;
+    if (c->cfg.method == VFMM_METHOD_DIRECT) {
+        D = 0;
+    } else if (c->cfg.depth > 0) {
+        D = c->cfg.depth;
+    } else {
+        double ratio = (double)n / (double)(c->cfg.ncrit > 0 ? c->cfg.ncrit : 64);
+        D = (int)std::lround(std::log(ratio > 1.0 ? ratio : 1.0) / std::log(8.0));
+        if (D < 1) D = 1;
+        if (D > MAX_DEPTH) D = MAX_DEPTH;
+    }
+    c->depth = D;
+    c->nside = 1 << D;
+    c->nleaf = (int64_t)1 << (3 * D);
+    c->leaf_w = c->cfg.box / c->nside;
+    c->n = n;
+    c->built = false;
+    const size_t esz = c->esz;
+    int st;
+    if ((st = ensure(c, c->xs, (size_t)n * 4 * esz, "positions"))) return st;
+    if ((st = ensure(c, c->gs, (size_t)n * 4 * esz, "strengths"))) return st;
+    if ((st = ensure(c, c->perm, (size_t)n * sizeof(int), "permutation"))) return st;
+    if ((st = ensure(c, c->keys, (size_t)n * sizeof(int), "keys"))) return st;
+    if ((st = ensure(c, c->tmpidx, (size_t)n * sizeof(int), "scatter"))) return st;
+    if ((st = ensure(c, c->counts, (size_t)c->nleaf * sizeof(int), "counts"))) return st;
+    if ((st = ensure(c, c->fill, (size_t)c->nleaf * sizeof(int), "fill"))) return st;
+    if ((st = ensure(c, c->leaf_start, (size_t)(c->nleaf + 1) * sizeof(int), "leaf ranges"))) return st;
+    if ((st = ensure(c, c->scan_part, (size_t)((c->nleaf + 1023) / 1024 + 1) * sizeof(int), "scan"))) return st;
+    if ((st = ensure(c, c->maxleaf, sizeof(int), "max leaf"))) return st;
+    if (c->cfg.method == VFMM_METHOD_FMM) {
+        c->lvl_off.assign(D + 2, 0);
+        size_t tot = 0;
+        for (int l = 0; l <= D; ++l) {
+            c->lvl_off[l] = tot;
+            tot += ((size_t)1 << (3 * l)) * 3 * c->pc;
+        }
+        c->lvl_off[D + 1] = tot;
+        if ((st = ensure(c, c->mexp, tot * esz, "multipoles"))) return st;
+        if ((st = ensure(c, c->lexp, tot * esz, "locals"))) return st;
+        if ((st = ensure(c, c->ufar, (size_t)n * 3 * esz, "far velocity"))) return st;
+        if ((st = ensure(c, c->sfar, (size_t)n * 3 * esz, "far stretching"))) return st;
+    }
+    cudaEventRecord(c->ev[0], c->stream);
+    if ((st = launch_tree(c, x))) return st;
+    cudaEventRecord(c->ev[1], c->stream);
+    int ml = 0;
+    cudaError_t e = cudaMemcpyAsync(&ml, c->maxleaf.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read leaf occupancy");
+    if ((st = check_device_error(c))) return st;
+    c->max_leaf = ml;
+    if (ml > LEAF_SORT_CAP)
+        return fail(c, VFMM_ERR_UNSUPPORTED, "a leaf holds more particles than the per-leaf sort capacity (4096); use a deeper tree");
+    c->built = true;
+    return VFMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vfmm_config_default(vfmm_config *cfg)
+{
+    if (!cfg) return VFMM_ERR_ARG;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->p = 10;
+    cfg->depth = 0;
+    cfg->ncrit = 64;
+    cfg->near_rings = 0;
+    cfg->rho_cut = 6.0;
+    cfg->periodic_levels = 2;
+    cfg->box = 6.283185307179586477;
+    cfg->dtype = VFMM_F32;
+    cfg->m2l_prec = VFMM_M2L_BF16X3;
+    cfg->method = VFMM_METHOD_FMM;
+    cfg->direct_images = 1;
+    cfg->stream = nullptr;
+    return VFMM_OK;
+}
+
+int vfmm_create(const vfmm_config *cfg, vfmm_handle *out)
+{
+    if (!out) return VFMM_ERR_ARG;
+    *out = nullptr;
+    if (!cfg) return VFMM_ERR_ARG;
+    const vfmm_config &k = *cfg;
+    if (k.dtype != VFMM_F32 && k.dtype != VFMM_F64) return VFMM_ERR_ARG;
+    if (k.method != VFMM_METHOD_FMM && k.method != VFMM_METHOD_DIRECT) return VFMM_ERR_ARG;
+    if (!(k.box > 0.0) || !std::isfinite(k.box)) return VFMM_ERR_ARG;
+    if (k.method == VFMM_METHOD_FMM) {
+        if (k.p < 2) return VFMM_ERR_ARG;
+        if ((k.p + 1) * (k.p + 1) > OUT_ROWS) return VFMM_ERR_UNSUPPORTED;
+        if (k.periodic_levels < 0 || k.periodic_levels > 8) return VFMM_ERR_ARG;
+        if (k.depth < 0 || k.depth > MAX_DEPTH) return VFMM_ERR_ARG;
+        if (k.near_rings < 0 || k.near_rings > 2) return VFMM_ERR_UNSUPPORTED;
+        if (!(k.rho_cut > 0.0)) return VFMM_ERR_ARG;
+        if (k.m2l_prec < VFMM_M2L_FP32 || k.m2l_prec > VFMM_M2L_BF16X3) return VFMM_ERR_ARG;
+        if (k.dtype == VFMM_F64 && k.m2l_prec != VFMM_M2L_FP64) return VFMM_ERR_ARG;
+        if (k.dtype == VFMM_F32 && k.m2l_prec == VFMM_M2L_FP64) return VFMM_ERR_ARG;
+    } else {
+        if (k.direct_images < 0 || k.direct_images > 20) return VFMM_ERR_ARG;
+    }
+    vfmm_ctx *h = new (std::nothrow) vfmm_ctx;
+    if (!h) return VFMM_ERR_OOM;
+    Ctx *c = &h->c;
+    c->cfg = k;
+    c->stream = (cudaStream_t)k.stream;
+    c->f64 = k.dtype == VFMM_F64;
+    c->esz = c->f64 ? 8 : 4;
+    c->p = k.method == VFMM_METHOD_FMM ? k.p : 2;
+    c->nc = (c->p + 1) * (c->p + 1);
+    c->pc = ((c->nc + 31) / 32) * 32;
+    for (int i = 0; i < 10; ++i) {
+        if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return VFMM_ERR_CUDA;
+        }
+    }
+    c->have_events = true;
+    int st = ensure(c, c->err, sizeof(int), "error word");
+    if (!st && cudaMemset(c->err.p, 0, sizeof(int)) != cudaSuccess) st = VFMM_ERR_CUDA;
+    if (!st && k.method == VFMM_METHOD_FMM) {
+        set_constants(c->p);
+        st = c->f64 ? build_operators<double>(c) : build_operators<float>(c);
+    }
+    if (st) {
+        vfmm_destroy(h);
+        return st;
+    }
+    *out = h;
+    return VFMM_OK;
+}
+
+int vfmm_destroy(vfmm_handle h)
+{
+    if (!h) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    cudaStreamSynchronize(c->stream);
+    DevBuf *bufs[] = {&c->xs, &c->gs, &c->perm, &c->keys, &c->leaf_start, &c->counts, &c->fill, &c->tmpidx,
+                      &c->scan_part, &c->err, &c->maxleaf, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->ufar,
+                      &c->sfar, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->m2m_f64,
+                      &c->lattice_f64, &c->root_m, &c->kblocks, &c->hx, &c->hg, &c->hu, &c->hs};
+    for (DevBuf *b : bufs) release(*b);
+    if (c->have_events)
+        for (int i = 0; i < 10; ++i) cudaEventDestroy(c->ev[i]);
+    delete h;
+    return VFMM_OK;
+}
+
+int vfmm_set_stream(vfmm_handle h, void *stream)
+{
+    if (!h) return VFMM_ERR_ARG;
+    h->c.stream = (cudaStream_t)stream;
+    h->c.cfg.stream = stream;
+    return VFMM_OK;
+}
+
+int vfmm_build_tree(vfmm_handle h, int64_t n, const void *x)
+{
+    if (!h) return VFMM_ERR_ARG;
+    return build_impl(&h->c, n, x);
+}
+
+int vfmm_eval_velocity_stretching(vfmm_handle h, const void *gamma, double sigma, void *u_out, void *s_out)
+{
+    if (!h) return VFMM_ERR_ARG;
+    return eval_impl(&h->c, gamma, sigma, u_out, s_out);
+}
+
+int vfmm_eval_host(vfmm_handle h, int64_t n, const void *x, const void *gamma, double sigma, void *u_out,
+                   void *s_out)
+{
+    if (!h) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    if (n <= 0 || !x || !gamma || !u_out) return fail(c, VFMM_ERR_ARG, "bad host arguments");
+    size_t bytes = (size_t)n * 3 * c->esz;
+    int st;
+    if ((st = ensure(c, c->hx, bytes, "host staging x"))) return st;
+    if ((st = ensure(c, c->hg, bytes, "host staging gamma"))) return st;
+    if ((st = ensure(c, c->hu, bytes, "host staging u"))) return st;
+    if ((st = ensure(c, c->hs, bytes, "host staging S"))) return st;
+    cudaError_t e = cudaMemcpyAsync(c->hx.p, x, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->hg.p, gamma, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host to device copy");
+    if ((st = build_impl(c, n, c->hx.p))) return st;
+    if ((st = eval_impl(c, c->hg.p, sigma, c->hu.p, s_out ? c->hs.p : nullptr))) return st;
+    e = cudaMemcpyAsync(u_out, c->hu.p, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && s_out) e = cudaMemcpyAsync(s_out, c->hs.p, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device to host copy");
+    return check_device_error(c);
+}
+
+int vfmm_sync(vfmm_handle h)
+{
+    if (!h) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    int st = check_device_error(c);
+    if (st) return st;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "asynchronous CUDA error");
+    return VFMM_OK;
+}
+
+int vfmm_get_timings(vfmm_handle h, double *ms, int nphase)
+{
+    if (!h || !ms || nphase < 0) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    if (!c->timed_eval) return fail(c, VFMM_ERR_NOT_BUILT, "no evaluation has been timed");
+    const int pairs[8][2] = {{0, 1}, {2, 3}, {3, 4}, {5, 6}, {4, 5}, {6, 7}, {7, 8}, {8, 9}};
+    for (int i = 0; i < nphase && i < NPHASE; ++i) {
+        float t = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&t, c->ev[pairs[i][0]], c->ev[pairs[i][1]]);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            t = 0.f;
+        }
+        ms[i] = t;
+    }
+    return VFMM_OK;
+}
+
+int vfmm_get_tree_info(vfmm_handle h, int64_t *out, int nout)
+{
+    if (!h || !out) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    int64_t v[5] = {c->depth, c->last_R, c->nside, c->max_leaf, c->n};
+    for (int i = 0; i < nout && i < 5; ++i) out[i] = v[i];
+    return VFMM_OK;
+}
+
+const char *vfmm_strerror(int status)
+{
+    switch (status) {
+    case VFMM_OK: return "ok";
+    case VFMM_ERR_ARG: return "invalid argument";
+    case VFMM_ERR_CUDA: return "CUDA error";
+    case VFMM_ERR_OOM: return "out of device memory";
+    case VFMM_ERR_NOT_BUILT: return "tree not built";
+    case VFMM_ERR_BOUNDS: return "device bounds check";
+    case VFMM_ERR_TIMEOUT: return "device wait timed out";
+    case VFMM_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+    }
+}
+
+const char *vfmm_last_error(vfmm_handle h)
+{
+    if (!h) return "null handle";
+    return h->c.last_error.c_str();
+}
+
+}  // extern "C"

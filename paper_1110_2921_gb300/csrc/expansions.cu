@@ -1,0 +1,644 @@
+// Expansion kernels of the periodic FMM: P2M, the gathered-column GEMM that performs M2M,
+// M2L and L2L on the CUDA cores, the FP64 root / periodic lattice step, and L2P.
+//
+// Section 3.1: the vector potential psi_c = sum_j gamma_{j,c} G (three scalar Laplace
+// potentials) is expanded in multipoles (Eq. fmm3dm) and locals (Eq. fmm3dl); velocity is
+// its curl (Eqs. biotsavartfmm1-2) and the stretching term uses its second derivatives
+// (Eqs. stretchingfmm1-2).  Coefficients use the balanced packed layout documented in
+// operators.cpp; every cell's block is [3][pc] (pc = padded coefficient stride).
+#include "common.cuh"
+#include "vfmm_internal.h"
+
+namespace vfmm {
+
+__constant__ float c_sfac_f[(PMAX + 1) * (PMAX + 1)];
+__constant__ double c_sfac_d[(PMAX + 1) * (PMAX + 1)];
+__constant__ float c_rec_f[(PMAX + 1) * (PMAX + 1)];   // 1/((n+m)(n-m)), n > m
+__constant__ double c_rec_d[(PMAX + 1) * (PMAX + 1)];
+__constant__ float c_inv2m_f[PMAX + 1];                // 1/(2m)
+__constant__ double c_inv2m_d[PMAX + 1];
+
+template <typename T> __device__ __forceinline__ T sfac_t(int n, int m);
+template <> __device__ __forceinline__ float sfac_t<float>(int n, int m) { return c_sfac_f[n * (PMAX + 1) + m]; }
+template <> __device__ __forceinline__ double sfac_t<double>(int n, int m) { return c_sfac_d[n * (PMAX + 1) + m]; }
+template <typename T> __device__ __forceinline__ T rec_t(int n, int m);
+template <> __device__ __forceinline__ float rec_t<float>(int n, int m) { return c_rec_f[n * (PMAX + 1) + m]; }
+template <> __device__ __forceinline__ double rec_t<double>(int n, int m) { return c_rec_d[n * (PMAX + 1) + m]; }
+template <typename T> __device__ __forceinline__ T inv2m_t(int m);
+template <> __device__ __forceinline__ float inv2m_t<float>(int m) { return c_inv2m_f[m]; }
+template <> __device__ __forceinline__ double inv2m_t<double>(int m) { return c_inv2m_d[m]; }
+
+void set_constants(int)
+{
+    float sf[(PMAX + 1) * (PMAX + 1)] = {0}, rf[(PMAX + 1) * (PMAX + 1)] = {0}, i2f[PMAX + 1] = {0};
+    double sd[(PMAX + 1) * (PMAX + 1)] = {0}, rd[(PMAX + 1) * (PMAX + 1)] = {0}, i2d[PMAX + 1] = {0};
+    for (int n = 0; n <= PMAX; ++n)
+        for (int m = 0; m <= n; ++m) {
+            sd[n * (PMAX + 1) + m] = ops::sfac(n, m);
+            sf[n * (PMAX + 1) + m] = (float)sd[n * (PMAX + 1) + m];
+            if (n > m) {
+                rd[n * (PMAX + 1) + m] = 1.0 / double((n + m) * (n - m));
+                rf[n * (PMAX + 1) + m] = (float)rd[n * (PMAX + 1) + m];
+            }
+        }
+    for (int m = 1; m <= PMAX; ++m) {
+        i2d[m] = 1.0 / (2.0 * m);
+        i2f[m] = (float)i2d[m];
+    }
+    cudaMemcpyToSymbol(c_sfac_f, sf, sizeof(sf));
+    cudaMemcpyToSymbol(c_sfac_d, sd, sizeof(sd));
+    cudaMemcpyToSymbol(c_rec_f, rf, sizeof(rf));
+    cudaMemcpyToSymbol(c_rec_d, rd, sizeof(rd));
+    cudaMemcpyToSymbol(c_inv2m_f, i2f, sizeof(i2f));
+    cudaMemcpyToSymbol(c_inv2m_d, i2d, sizeof(i2d));
+}
+
+__device__ __forceinline__ int pk(int n, int m) { return m == 0 ? n * n : n * n + 2 * m - 1; }
+
+// ---------------------------------------------------------------------------------------
+// gamma gather: gs[pos] = gamma[perm[pos]] in the compute type
+template <typename T>
+__global__ void k_gather_gamma(int64_t n, const T *__restrict__ g, const int *__restrict__ perm,
+                               typename V4<T>::type *__restrict__ gs)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t s = perm[i];
+    gs[i] = make_v4<T>(g[3 * s], g[3 * s + 1], g[3 * s + 2], T(0));
+}
+
+int launch_gather_gamma(Ctx *c, const void *gamma)
+{
+    int nb = (int)((c->n + 255) / 256);
+    if (c->f64)
+        k_gather_gamma<double><<<nb, 256, 0, c->stream>>>(c->n, (const double *)gamma, (const int *)c->perm.p,
+                                                          (dvec4 *)c->gs.p);
+    else
+        k_gather_gamma<float><<<nb, 256, 0, c->stream>>>(c->n, (const float *)gamma, (const int *)c->perm.p,
+                                                        (float4 *)c->gs.p);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// P2M (Eq. fmm3dm): Mh_n^m = s_nm sum_j gamma_j Y_n^m((x_j - z)/w) for each leaf.
+constexpr int P2M_TP = 32;
+constexpr int P2M_BS = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(P2M_BS) k_p2m(const typename V4<T>::type *__restrict__ xs,
+                                                const typename V4<T>::type *__restrict__ gs,
+                                                const int *__restrict__ ls, int nside, int log2n, T w, int p, int pc,
+                                                T *__restrict__ M)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Ysm = (T *)smem_raw;                 // [P2M_TP][pc]
+    T *gsm = Ysm + P2M_TP * pc;             // [P2M_TP][3]
+    const int leaf = blockIdx.x;
+    const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
+    const T zx = (cx + T(0.5)) * w, zy = (cy + T(0.5)) * w, zz = (cz + T(0.5)) * w;
+    const T invw = T(1) / w;
+    const int b = ls[leaf], e = ls[leaf + 1];
+    const int nout = 3 * pc;
+    T acc[4] = {0, 0, 0, 0};  // outputs tid + k * P2M_BS, 3*pc <= 4*P2M_BS for p <= 16 with pc <= 170
+    for (int s0 = b; s0 < e; s0 += P2M_TP) {
+        int cnt = min(P2M_TP, e - s0);
+        if (threadIdx.x < P2M_TP) {
+            T *row = Ysm + threadIdx.x * pc;
+            if (threadIdx.x < cnt) {
+                typename V4<T>::type xp = xs[s0 + threadIdx.x];
+                typename V4<T>::type gp = gs[s0 + threadIdx.x];
+                gsm[3 * threadIdx.x + 0] = gp.x;
+                gsm[3 * threadIdx.x + 1] = gp.y;
+                gsm[3 * threadIdx.x + 2] = gp.z;
+                T x = (xp.x - zx) * invw, y = (xp.y - zy) * invw, z = (xp.z - zz) * invw;
+                T r2 = x * x + y * y + z * z;
+                T dre = 1, dim = 0;
+                for (int m = 0; m <= p; ++m) {
+                    if (m > 0) {
+                        T f = -inv2m_t<T>(m);
+                        T nre = f * (x * dre - y * dim);
+                        T nim = f * (x * dim + y * dre);
+                        dre = nre;
+                        dim = nim;
+                    }
+                    T s = sfac_t<T>(m, m);
+                    row[pk(m, m)] = dre * s;
+                    if (m > 0) row[pk(m, m) + 1] = dim * s;
+                    T pre = dre, pim = dim, ppre = 0, ppim = 0;
+                    for (int n = m + 1; n <= p; ++n) {
+                        T c1 = T(2 * n - 1) * z, f = rec_t<T>(n, m);
+                        T cre = (c1 * pre - r2 * ppre) * f;
+                        T cim = (c1 * pim - r2 * ppim) * f;
+                        T sn = sfac_t<T>(n, m);
+                        row[pk(n, m)] = cre * sn;
+                        if (m > 0) row[pk(n, m) + 1] = cim * sn;
+                        ppre = pre;
+                        ppim = pim;
+                        pre = cre;
+                        pim = cim;
+                    }
+                }
+                for (int j = (p + 1) * (p + 1); j < pc; ++j) row[j] = 0;
+            } else {
+                for (int j = 0; j < pc; ++j) row[j] = 0;
+                gsm[3 * threadIdx.x + 0] = 0;
+                gsm[3 * threadIdx.x + 1] = 0;
+                gsm[3 * threadIdx.x + 2] = 0;
+            }
+        }
+        __syncthreads();
+        for (int k = 0; k < 4; ++k) {
+            int o = threadIdx.x + k * P2M_BS;
+            if (o < nout) {
+                int comp = o / pc, j = o - comp * pc;
+                T s = 0;
+                for (int t = 0; t < cnt; ++t) s += gsm[3 * t + comp] * Ysm[t * pc + j];
+                acc[k] += s;
+            }
+        }
+        __syncthreads();
+    }
+    for (int k = 0; k < 4; ++k) {
+        int o = threadIdx.x + k * P2M_BS;
+        if (o < nout) M[(size_t)leaf * nout + o] = acc[k];
+    }
+}
+
+int launch_p2m(Ctx *c)
+{
+    int log2n = 0;
+    while ((1 << log2n) < c->nside) ++log2n;
+    size_t off = c->lvl_off[c->depth];
+    size_t sm = (size_t)P2M_TP * c->pc * c->esz + P2M_TP * 3 * c->esz;
+    if (c->f64)
+        k_p2m<double><<<(unsigned)c->nleaf, P2M_BS, sm, c->stream>>>(
+            (const dvec4 *)c->xs.p, (const dvec4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,
+            c->leaf_w, c->p, c->pc, (double *)c->mexp.p + off);
+    else
+        k_p2m<float><<<(unsigned)c->nleaf, P2M_BS, sm, c->stream>>>(
+            (const float4 *)c->xs.p, (const float4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,
+            (float)c->leaf_w, c->p, c->pc, (float *)c->mexp.p + off);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Gathered-column GEMM on the CUDA cores.
+// Output tile: 128 coefficient rows x 96 columns (32 target cells x 3 components), 256
+// threads, 8x6 register block per thread, K chunks staged in shared memory with register
+// double buffering.  The K loop runs over k-blocks (one translation matrix each) and the
+// columns of each k-block are gathered from the source cell of that k-block.
+constexpr int GM = 128, GN = 96, GCELLS = 32, GTHREADS = 256;
+
+template <typename T> struct GemmCfg;
+template <> struct GemmCfg<float> {
+    static constexpr int BK = 16;
+    typedef float4 vec;
+    static constexpr int VEC = 4;
+};
+template <> struct GemmCfg<double> {
+    static constexpr int BK = 8;
+    typedef double2 vec;
+    static constexpr int VEC = 2;
+};
+
+__device__ __forceinline__ void target_cell(const GemmParams &gp, int g, int64_t q, int &cx, int &cy, int &cz)
+{
+    if (gp.grouped) {
+        int h = gp.n_tgt >> 1;
+        int px = (int)(q / ((int64_t)h * h)), py = (int)((q / h) % h), pz = (int)(q % h);
+        cx = 2 * px + ((g >> 2) & 1);
+        cy = 2 * py + ((g >> 1) & 1);
+        cz = 2 * pz + (g & 1);
+    } else {
+        int n = gp.n_tgt;
+        cx = (int)(q / ((int64_t)n * n));
+        cy = (int)((q / n) % n);
+        cz = (int)(q % n);
+    }
+}
+
+__device__ __forceinline__ int64_t source_cell(const GemmParams &gp, int cx, int cy, int cz, int4 kb)
+{
+    int sx, sy, sz, n = gp.n_src;
+    if (gp.mode == 0) {
+        sx = (cx + kb.y) & (n - 1);
+        sy = (cy + kb.z) & (n - 1);
+        sz = (cz + kb.w) & (n - 1);
+    } else if (gp.mode == 1) {
+        sx = 2 * cx + kb.y;
+        sy = 2 * cy + kb.z;
+        sz = 2 * cz + kb.w;
+    } else {
+        sx = cx >> 1;
+        sy = cy >> 1;
+        sz = cz >> 1;
+    }
+    return ((int64_t)sx * n + sy) * n + sz;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GTHREADS) k_gemm(GemmParams gp, int64_t ncell_group)
+{
+    typedef GemmCfg<T> C;
+    constexpr int BK = C::BK, VEC = C::VEC;
+    typedef typename C::vec vec;
+    __shared__ __align__(16) T As[2][BK][GM];
+    __shared__ __align__(16) T Bs[2][BK][GN];
+    const int g = gp.grouped ? blockIdx.y : 0;
+    const int tid = threadIdx.x;
+    const int tm = tid >> 4, tn = tid & 15;
+    const int64_t cell0 = (int64_t)blockIdx.x * GCELLS;
+    const int nkb = gp.kb_cnt[g];
+    const int4 *kbl = gp.kb + gp.kb_off[g];
+    const int pc = gp.pc;
+    const int nch = pc / BK;
+    const int total = nkb * nch;
+    const T *AT = (const T *)gp.AT;
+    const T *B = (const T *)gp.B;
+
+    // B-load slots of this thread: v = tid and tid + 256 (< 384 = GN * BK / VEC)
+    int slot_n[2], slot_part[2], slot_comp[2], slot_cx[2], slot_cy[2], slot_cz[2];
+    bool slot_ok[2];
+    for (int s = 0; s < 2; ++s) {
+        int v = tid + s * GTHREADS;
+        slot_ok[s] = v < GN * BK / VEC;
+        int part = v / GN, n = v - part * GN;
+        slot_part[s] = part;
+        slot_n[s] = n;
+        int q = n / 3;
+        slot_comp[s] = n - 3 * q;
+        int64_t cq = cell0 + q;
+        if (cq >= ncell_group) slot_ok[s] = false;
+        int cx = 0, cy = 0, cz = 0;
+        if (slot_ok[s]) target_cell(gp, g, cq, cx, cy, cz);
+        slot_cx[s] = cx;
+        slot_cy[s] = cy;
+        slot_cz[s] = cz;
+        if (v >= GN * BK / VEC) slot_n[s] = -1;
+    }
+
+    T acc[8][6];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc[i][j] = 0;
+
+    vec ra[2], rb[2];
+    auto load = [&](int c) {
+        int kbi = c / nch, j0 = (c - kbi * nch) * BK;
+        int4 kb = kbl[kbi];
+        const T *a = AT + ((size_t)kb.x * pc + j0) * GM;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) ra[s] = ((const vec *)a)[tid + s * GTHREADS];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (slot_ok[s]) {
+                int64_t src = source_cell(gp, slot_cx[s], slot_cy[s], slot_cz[s], kb);
+                rb[s] = *(const vec *)(B + (src * 3 + slot_comp[s]) * pc + j0 + slot_part[s] * VEC);
+            } else {
+                T *z = (T *)&rb[s];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) z[e] = 0;
+            }
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            int v = tid + s * GTHREADS;  // A: v indexes 16-byte vectors of As[buf] in order
+            ((vec *)&As[buf][0][0])[v] = ra[s];
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (slot_n[s] >= 0) {
+                const T *z = (const T *)&rb[s];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) Bs[buf][slot_part[s] * VEC + e][slot_n[s]] = z[e];
+            }
+        }
+    };
+
+    if (total > 0) {
+        load(0);
+        store(0);
+    }
+    __syncthreads();
+    for (int c = 0; c < total; ++c) {
+        int buf = c & 1;
+        if (c + 1 < total) load(c + 1);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[8], b[6];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = As[buf][kk][tm * 8 + i];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) b[j] = Bs[buf][kk][tn * 6 + j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 6; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        if (c + 1 < total) store(buf ^ 1);
+        __syncthreads();
+    }
+    // epilogue
+    T *Cp = (T *)gp.C;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        int n = tn * 6 + j;
+        int q = n / 3, comp = n - 3 * q;
+        int64_t cq = cell0 + q;
+        if (cq >= ncell_group) continue;
+        int cx, cy, cz;
+        target_cell(gp, g, cq, cx, cy, cz);
+        int64_t cell = ((int64_t)cx * gp.n_tgt + cy) * gp.n_tgt + cz;
+        T *row = Cp + (cell * 3 + comp) * pc;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int m = tm * 8 + i;
+            if (m < pc) row[m] = gp.accumulate ? row[m] + acc[i][j] : acc[i][j];
+        }
+    }
+}
+
+int launch_gemm(Ctx *c, const GemmParams &gp, int ngroups, int64_t ncell_group)
+{
+    if (ncell_group <= 0) return VFMM_OK;
+    dim3 grid((unsigned)((ncell_group + GCELLS - 1) / GCELLS), (unsigned)ngroups);
+    if (c->f64)
+        k_gemm<double><<<grid, GTHREADS, 0, c->stream>>>(gp, ncell_group);
+    else
+        k_gemm<float><<<grid, GTHREADS, 0, c->stream>>>(gp, ncell_group);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Root step in FP64: M_0 = sum_b M2M_b M_1[b]; L_0 = Op M_0 with Op the periodic lattice
+// operator (images outside the central 3^3 boxes; Section 3.1 last paragraph).
+template <typename T>
+__global__ void k_root(const T *__restrict__ M1, const double *__restrict__ m2m, const double *__restrict__ op,
+                       int nc, int pc, double *__restrict__ root_m, T *__restrict__ L0)
+{
+    extern __shared__ double rm[];  // [3][nc]
+    for (int o = threadIdx.x; o < 3 * nc; o += blockDim.x) {
+        int comp = o / nc, k = o - comp * nc;
+        double s = 0.0;
+        for (int b = 0; b < 8; ++b) {
+            const double *A = m2m + ((size_t)b * nc + k) * nc;
+            const T *x = M1 + ((size_t)b * 3 + comp) * pc;
+            for (int j = 0; j < nc; ++j) s += A[j] * (double)x[j];
+        }
+        rm[o] = s;
+        root_m[o] = s;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < 3 * pc; o += blockDim.x) {
+        int comp = o / pc, k = o - comp * pc;
+        double s = 0.0;
+        if (k < nc) {
+            const double *A = op + (size_t)k * nc;
+            for (int j = 0; j < nc; ++j) s += A[j] * rm[comp * nc + j];
+        }
+        L0[o] = (T)s;
+    }
+}
+
+int launch_root(Ctx *c)
+{
+    size_t sm = 3 * c->nc * sizeof(double);
+    if (c->f64)
+        k_root<double><<<1, 384, sm, c->stream>>>((const double *)c->mexp.p + c->lvl_off[1],
+                                                  (const double *)c->m2m_f64.p, (const double *)c->lattice_f64.p,
+                                                  c->nc, c->pc, (double *)c->root_m.p, (double *)c->lexp.p);
+    else
+        k_root<float><<<1, 384, sm, c->stream>>>((const float *)c->mexp.p + c->lvl_off[1],
+                                                 (const double *)c->m2m_f64.p, (const double *)c->lattice_f64.p,
+                                                 c->nc, c->pc, (double *)c->root_m.p, (float *)c->lexp.p);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// L2P (Eqs. biotsavartfmm2, stretchingfmm2): gradient and Hessian of the three local
+// expansions at each particle.  Per leaf, the coefficient vectors of d_a psi and
+// d_a d_b psi are formed from the local coefficients with
+//   d_z Y_n^m = Y_{n-1}^m, (d_x + i d_y) Y_n^m = Y_{n-1}^{m+1}, (d_x - i d_y) Y_n^m = -Y_{n-1}^{m-1},
+// i.e. for psi = sum conj(Y_k^l) F_k^l:
+//   G^z_{a,b} = F_{a+1,b},  G^x_{a,b} = (F_{a+1,b-1} - F_{a+1,b+1})/2,
+//   G^y_{a,b} = i (F_{a+1,b+1} + F_{a+1,b-1})/2.
+// Each particle then evaluates Y_a^b at its offset once and accumulates 27 dot products.
+constexpr int L2P_BS = 128;
+
+template <typename T> struct Cx {
+    T re, im;
+};
+
+template <typename T> __device__ __forceinline__ Cx<T> getc(const T *P, int n, int m, int nmax)
+{
+    Cx<T> z = {0, 0};
+    if (n < 0 || n > nmax) return z;
+    int am = m < 0 ? -m : m;
+    if (am > n) return z;
+    if (am == 0) {
+        z.re = P[n * n];
+        return z;
+    }
+    z.re = P[n * n + 2 * am - 1];
+    z.im = P[n * n + 2 * am];
+    if (m < 0) {  // (-1)^m conj
+        z.im = -z.im;
+        if (am & 1) {
+            z.re = -z.re;
+            z.im = -z.im;
+        }
+    }
+    return z;
+}
+
+// out = D^dir(in) for degrees 0..nmax-1 (in has degrees 0..nmax); dir 0 = x, 1 = y, 2 = z.
+template <typename T> __device__ __forceinline__ void deriv_store(const T *in, int nmax, int dir, int a, int b, T *out)
+{
+    Cx<T> v;
+    if (dir == 2) {
+        v = getc(in, a + 1, b, nmax);
+    } else {
+        Cx<T> p1 = getc(in, a + 1, b + 1, nmax), m1 = getc(in, a + 1, b - 1, nmax);
+        if (dir == 0) {
+            v.re = T(0.5) * (m1.re - p1.re);
+            v.im = T(0.5) * (m1.im - p1.im);
+        } else {
+            // i/2 (p1 + m1)
+            v.re = T(-0.5) * (p1.im + m1.im);
+            v.im = T(0.5) * (p1.re + m1.re);
+        }
+    }
+    out[pk(a, b)] = v.re;
+    if (b > 0) out[pk(a, b) + 1] = v.im;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__restrict__ xs,
+                                                const typename V4<T>::type *__restrict__ gs,
+                                                const int *__restrict__ ls, int nside, int log2n, T w, int p, int pc,
+                                                const T *__restrict__ Lc, T *__restrict__ ufar, T *__restrict__ sfar)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *F = (T *)smem_raw;            // [3][pc]
+    T *G = F + 3 * pc;               // [3 dir][3 comp][pc]
+    T *H = G + 9 * pc;               // [6 pair][3 comp][pc]
+    const int leaf = blockIdx.x;
+    const int b0 = ls[leaf], e0 = ls[leaf + 1];
+    if (e0 <= b0) return;
+    const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
+    const int nc = (p + 1) * (p + 1);
+    for (int o = threadIdx.x; o < 3 * pc; o += blockDim.x) {
+        int comp = o / pc, j = o - comp * pc;
+        T v = 0;
+        if (j < nc) {
+            int n = 0;
+            while ((n + 1) * (n + 1) <= j) ++n;
+            int r = j - n * n, m = (r + 1) >> 1;
+            v = Lc[(size_t)leaf * 3 * pc + o] * sfac_t<T>(n, m);
+        }
+        F[o] = v;
+    }
+    __syncthreads();
+    const int npair1 = p * (p + 1) / 2;  // (a, b) with a < p
+    for (int it = threadIdx.x; it < 9 * npair1; it += blockDim.x) {
+        int q = it % npair1, rest = it / npair1;
+        int comp = rest % 3, dir = rest / 3;
+        int a = 0;
+        while ((a + 1) * (a + 2) / 2 <= q) ++a;
+        int bb = q - a * (a + 1) / 2;
+        deriv_store<T>(F + comp * pc, p, dir, a, bb, G + (dir * 3 + comp) * pc);
+    }
+    __syncthreads();
+    const int npair2 = (p - 1) * p / 2;  // (a, b) with a < p - 1
+    const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+    for (int it = threadIdx.x; it < 18 * npair2; it += blockDim.x) {
+        int q = it % npair2, rest = it / npair2;
+        int comp = rest % 3, pr = rest / 3;
+        int a = 0;
+        while ((a + 1) * (a + 2) / 2 <= q) ++a;
+        int bb = q - a * (a + 1) / 2;
+        deriv_store<T>(G + (pa[pr] * 3 + comp) * pc, p - 1, pb[pr], a, bb, H + (pr * 3 + comp) * pc);
+    }
+    __syncthreads();
+    const T zx = (cx + T(0.5)) * w, zy = (cy + T(0.5)) * w, zz = (cz + T(0.5)) * w;
+    const T invw = T(1) / w;
+    for (int i = b0 + threadIdx.x; i < e0; i += blockDim.x) {
+        typename V4<T>::type xp = xs[i];
+        T x = (xp.x - zx) * invw, y = (xp.y - zy) * invw, z = (xp.z - zz) * invw;
+        T r2 = x * x + y * y + z * z;
+        T gr[3][3], hs[3][6];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gr[a][k] = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) hs[a][k] = 0;
+        T dre = 1, dim = 0;
+        for (int m = 0; m < p; ++m) {
+            if (m > 0) {
+                T f = -inv2m_t<T>(m);
+                T nre = f * (x * dre - y * dim);
+                T nim = f * (x * dim + y * dre);
+                dre = nre;
+                dim = nim;
+            }
+            T pre = dre, pim = dim, ppre = 0, ppim = 0;
+            for (int n = m; n < p; ++n) {
+                T cre, cim;
+                if (n == m) {
+                    cre = dre;
+                    cim = dim;
+                } else {
+                    T c1 = T(2 * n - 1) * z, f = rec_t<T>(n, m);
+                    cre = (c1 * pre - r2 * ppre) * f;
+                    cim = (c1 * pim - r2 * ppim) * f;
+                    ppre = pre;
+                    ppim = pim;
+                    pre = cre;
+                    pim = cim;
+                }
+                // sum_b conj(Y) G over b = +-m: weight 2 for m > 0 (real part of conj(Y) G)
+                T wre = m > 0 ? T(2) * cre : cre, wim = m > 0 ? T(2) * cim : T(0);
+                int j = pk(n, m);
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int comp = 0; comp < 3; ++comp) {
+                        const T *Gv = G + (d * 3 + comp) * pc + j;
+                        T acc = wre * Gv[0];
+                        if (m > 0) acc += wim * Gv[1];
+                        gr[comp][d] += acc;
+                    }
+                if (n < p - 1) {
+#pragma unroll
+                    for (int pr = 0; pr < 6; ++pr)
+#pragma unroll
+                        for (int comp = 0; comp < 3; ++comp) {
+                            const T *Hv = H + (pr * 3 + comp) * pc + j;
+                            T acc = wre * Hv[0];
+                            if (m > 0) acc += wim * Hv[1];
+                            hs[comp][pr] += acc;
+                        }
+                }
+            }
+        }
+        // psi_c = (1/4pi)(1/w) sum conj(Y) s F; d/dx = (1/w) d/dy
+        const T s1 = T(0.0795774715459476679) * invw * invw;
+        const T s2 = s1 * invw;
+        // gr[c][a] = d_a psi_c ; hs[c][pair] = d_a d_b psi_c with pairs xx xy xz yy yz zz
+        T u0 = s1 * (gr[2][1] - gr[1][2]);
+        T u1 = s1 * (gr[0][2] - gr[2][0]);
+        T u2 = s1 * (gr[1][0] - gr[0][1]);
+        typename V4<T>::type gp = gs[i];
+        T gk[3] = {gp.x, gp.y, gp.z};
+        // H(c, k, b) = d_k d_b psi_c
+        auto Hc = [&](int comp, int k, int b) -> T {
+            int lo = k < b ? k : b, hi = k < b ? b : k;
+            int idx = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+            return hs[comp][idx];
+        };
+        T S0 = 0, S1 = 0, S2 = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            S0 += gk[k] * (Hc(2, k, 1) - Hc(1, k, 2));
+            S1 += gk[k] * (Hc(0, k, 2) - Hc(2, k, 0));
+            S2 += gk[k] * (Hc(1, k, 0) - Hc(0, k, 1));
+        }
+        ufar[3 * (int64_t)i + 0] = u0;
+        ufar[3 * (int64_t)i + 1] = u1;
+        ufar[3 * (int64_t)i + 2] = u2;
+        sfar[3 * (int64_t)i + 0] = s2 * S0;
+        sfar[3 * (int64_t)i + 1] = s2 * S1;
+        sfar[3 * (int64_t)i + 2] = s2 * S2;
+    }
+}
+
+int launch_l2p(Ctx *c)
+{
+    int log2n = 0;
+    while ((1 << log2n) < c->nside) ++log2n;
+    size_t off = c->lvl_off[c->depth];
+    size_t sm = (size_t)(3 + 9 + 18) * c->pc * c->esz;
+    if (c->f64)
+        k_l2p<double><<<(unsigned)c->nleaf, L2P_BS, sm, c->stream>>>(
+            (const dvec4 *)c->xs.p, (const dvec4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,
+            c->leaf_w, c->p, c->pc, (const double *)c->lexp.p + off, (double *)c->ufar.p, (double *)c->sfar.p);
+    else
+        k_l2p<float><<<(unsigned)c->nleaf, L2P_BS, sm, c->stream>>>(
+            (const float4 *)c->xs.p, (const float4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,
+            (float)c->leaf_w, c->p, c->pc, (const float *)c->lexp.p + off, (float *)c->ufar.p,
+            (float *)c->sfar.p);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+}  // namespace vfmm

@@ -1,0 +1,196 @@
+// Uniform periodic octree: wrap, leaf key, counting sort, per-leaf index sort, gather.
+//
+// The paper builds its tree on the CPU (Section 2.2); here every step runs on the GPU.
+// Keys are row-major leaf indices (ix * n + iy) * n + iz at depth D.  The sort is a counting
+// sort (atomic histogram, three-kernel exclusive scan, atomic scatter) followed by a sort of
+// each leaf's particle indices, which makes the final order deterministic: within a leaf,
+// particles appear in increasing caller index.
+#include "common.cuh"
+#include "vfmm_internal.h"
+
+#include <climits>
+
+namespace vfmm {
+
+template <typename TIn>
+__global__ void k_keys(int64_t n, const TIn *__restrict__ x, int nside, double L, int *__restrict__ keys,
+                       int *__restrict__ counts)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double invL = 1.0 / L;
+    int c[3];
+    for (int d = 0; d < 3; ++d) {
+        double v = wrap_coord<double>((double)x[3 * i + d], L, invL);
+        int ci = (int)(v * invL * nside);
+        c[d] = ci < 0 ? 0 : (ci >= nside ? nside - 1 : ci);
+    }
+    int key = (c[0] * nside + c[1]) * nside + c[2];
+    keys[i] = key;
+    atomicAdd(&counts[key], 1);
+}
+
+// Exclusive scan, level 1: each block scans 1024 counts, writes local prefix and its total.
+__global__ void k_scan_blocks(int64_t nleaf, const int *__restrict__ counts, int *__restrict__ out,
+                              int *__restrict__ part, int *__restrict__ maxleaf)
+{
+    __shared__ int s[1024];
+    __shared__ int smax[32];
+    int64_t base = (int64_t)blockIdx.x * 1024;
+    int t = threadIdx.x;  // 256 threads, 4 items each
+    int v[4];
+    int loc = 0, mx = 0;
+    for (int k = 0; k < 4; ++k) {
+        int64_t idx = base + 4 * t + k;
+        v[k] = idx < nleaf ? counts[idx] : 0;
+        loc += v[k];
+        mx = max(mx, v[k]);
+    }
+    s[t] = loc;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        int add = t >= off ? s[t - off] : 0;
+        __syncthreads();
+        s[t] += add;
+        __syncthreads();
+    }
+    int excl = s[t] - loc;
+    for (int k = 0; k < 4; ++k) {
+        int64_t idx = base + 4 * t + k;
+        if (idx < nleaf) out[idx] = excl;
+        excl += v[k];
+    }
+    if (t == 255) part[blockIdx.x] = s[255];
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((t & 31) == 0) smax[t >> 5] = mx;
+    __syncthreads();
+    if (t == 0) {
+        int m = 0;
+        for (int w = 0; w < 8; ++w) m = max(m, smax[w]);
+        atomicMax(maxleaf, m);
+    }
+}
+
+// Level 2: one block scans the block totals (sequential chunks per thread).
+__global__ void k_scan_parts(int nparts, int *__restrict__ part, int *__restrict__ total)
+{
+    __shared__ int s[1024];
+    int t = threadIdx.x;
+    int per = (nparts + 1023) / 1024;
+    int loc = 0;
+    for (int k = 0; k < per; ++k) {
+        int idx = t * per + k;
+        if (idx < nparts) loc += part[idx];
+    }
+    s[t] = loc;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int add = t >= off ? s[t - off] : 0;
+        __syncthreads();
+        s[t] += add;
+        __syncthreads();
+    }
+    int excl = s[t] - loc;
+    for (int k = 0; k < per; ++k) {
+        int idx = t * per + k;
+        if (idx < nparts) {
+            int v = part[idx];
+            part[idx] = excl;
+            excl += v;
+        }
+    }
+    if (t == 1023) *total = s[1023];
+}
+
+__global__ void k_scan_add(int64_t nleaf, int *__restrict__ out, const int *__restrict__ part)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < nleaf) out[idx] += part[idx / 1024];
+}
+
+__global__ void k_scatter(int64_t n, const int *__restrict__ keys, const int *__restrict__ start,
+                          int *__restrict__ fill, int *__restrict__ tmpidx)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = keys[i];
+    int pos = start[k] + atomicAdd(&fill[k], 1);
+    tmpidx[pos] = (int)i;
+}
+
+// One block per leaf: bitonic sort of the leaf's indices in shared memory, then write the
+// permutation and the wrapped, sorted positions.
+template <typename TIn, typename T>
+__global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict__ tmpidx, const TIn *__restrict__ x,
+                            double L, int *__restrict__ perm, typename V4<T>::type *__restrict__ xs,
+                            int *__restrict__ err)
+{
+    __shared__ int s[LEAF_SORT_CAP];
+    int leaf = blockIdx.x;
+    int b = start[leaf], e = start[leaf + 1];
+    int cnt = e - b;
+    if (cnt <= 0) return;
+    if (cnt > LEAF_SORT_CAP) {
+        if (threadIdx.x == 0) atomicOr(err, ERRBIT_LEAF_OVERFLOW);
+        return;
+    }
+    int m = 1;
+    while (m < cnt) m <<= 1;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) s[k] = k < cnt ? tmpidx[b + k] : INT_MAX;
+    __syncthreads();
+    for (int size = 2; size <= m; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int k = threadIdx.x; k < m; k += blockDim.x) {
+                int q = k ^ stride;
+                if (q > k) {
+                    bool up = (k & size) == 0;
+                    int a = s[k], c = s[q];
+                    if ((a > c) == up) {
+                        s[k] = c;
+                        s[q] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    double invL = 1.0 / L;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        int i = s[k];
+        perm[b + k] = i;
+        T c0 = (T)wrap_coord<double>((double)x[3 * (int64_t)i + 0], L, invL);
+        T c1 = (T)wrap_coord<double>((double)x[3 * (int64_t)i + 1], L, invL);
+        T c2 = (T)wrap_coord<double>((double)x[3 * (int64_t)i + 2], L, invL);
+        xs[b + k] = make_v4<T>(c0, c1, c2, T(0));
+    }
+}
+
+template <typename TIn, typename T> static int tree_impl(Ctx *c, const TIn *x)
+{
+    cudaStream_t st = c->stream;
+    int64_t n = c->n, nleaf = c->nleaf;
+    cudaMemsetAsync(c->counts.p, 0, nleaf * sizeof(int), st);
+    cudaMemsetAsync(c->fill.p, 0, nleaf * sizeof(int), st);
+    cudaMemsetAsync(c->maxleaf.p, 0, sizeof(int), st);
+    int nb = (int)((n + 255) / 256);
+    k_keys<TIn><<<nb, 256, 0, st>>>(n, x, c->nside, c->cfg.box, (int *)c->keys.p, (int *)c->counts.p);
+    int nparts = (int)((nleaf + 1023) / 1024);
+    int *start = (int *)c->leaf_start.p;
+    int *part = (int *)c->scan_part.p;
+    k_scan_blocks<<<nparts, 256, 0, st>>>(nleaf, (int *)c->counts.p, start, part, (int *)c->maxleaf.p);
+    k_scan_parts<<<1, 1024, 0, st>>>(nparts, part, start + nleaf);
+    k_scan_add<<<(int)((nleaf + 255) / 256), 256, 0, st>>>(nleaf, start, part);
+    k_scatter<<<nb, 256, 0, st>>>(n, (int *)c->keys.p, start, (int *)c->fill.p, (int *)c->tmpidx.p);
+    k_leaf_sort<TIn, T><<<(unsigned)nleaf, 256, 0, st>>>(start, (int *)c->tmpidx.p, x, c->cfg.box,
+                                                         (int *)c->perm.p,
+                                                         (typename V4<T>::type *)c->xs.p, (int *)c->err.p);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+int launch_tree(Ctx *c, const void *x)
+{
+    if (c->f64) return tree_impl<double, double>(c, (const double *)x);
+    return tree_impl<float, float>(c, (const float *)x);
+}
+
+}  // namespace vfmm

@@ -1,0 +1,121 @@
+// Internal declarations shared by the translation units of libvfmm.
+#pragma once
+
+#include "vfmm.h"
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace vfmm {
+
+constexpr int PMAX = 16;          // largest supported expansion order
+constexpr int NPHASE = 8;         // timed phases (see vfmm_get_timings)
+constexpr int MAX_DEPTH = 8;      // deepest octree level
+constexpr int LEAF_SORT_CAP = 4096;  // per-leaf index sort capacity
+constexpr int OUT_ROWS = 128;     // rows of every packed translation matrix (output coefficients, padded)
+constexpr int NT = 343;           // M2L offsets t in [-3,3]^3
+
+// device error word bits
+constexpr int ERRBIT_LEAF_OVERFLOW = 1;
+constexpr int ERRBIT_BOUNDS = 2;
+constexpr int ERRBIT_TIMEOUT = 4;
+
+namespace ops {
+double sfac(int n, int m);
+std::vector<double> m2l_hat(const double t[3], int p);
+std::vector<double> m2m_hat(const double e[3], double ratio, int p);
+std::vector<double> l2l_hat(const double e[3], int p);
+std::vector<double> lattice_operator(int p, int S);
+}  // namespace ops
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Parameters of the gathered-column GEMM used by M2M, M2L and L2L on the CUDA cores.
+// C[cell_t][comp][k] (+)= sum_{kblocks} sum_j AT[mat][j][k] * B[src(cell_t, t)][comp][j]
+struct GemmParams {
+    const void *AT;   // [nmat][pc][OUT_ROWS] transposed matrices (input-major)
+    const void *B;    // source coefficient rows [ncell_src][3][pc]
+    void *C;          // target rows [ncell_tgt][3][pc]
+    const int4 *kb;   // k-blocks (mat, tx, ty, tz)
+    int kb_off[8];    // per target parity group: first k-block
+    int kb_cnt[8];    // per target parity group: number of k-blocks
+    int n_src;        // cells per side at the source level
+    int n_tgt;        // cells per side at the target level
+    int mode;         // 0 = M2L (src = wrap(c + t)), 1 = M2M (src = 2c + t), 2 = L2L (src = c >> 1)
+    int grouped;      // 1: targets split by parity (grid.y = 8); 0: all cells
+    int accumulate;   // C += instead of C =
+    int pc;           // padded coefficient stride (multiple of 16)
+};
+
+struct TcParams {
+    const void *Ahi, *Alo;  // [NT][nchunk][tile bytes] pre-tiled translation matrices
+    const void *Bhi, *Blo;  // multipole hi/lo rows [ncell][3][pc] (bf16 or tf32-in-fp32)
+    float *C;               // local rows [ncell][3][pc] (FP32), stored
+    const int4 *kb;
+    int kb_off[8], kb_cnt[8];
+    int n;                  // cells per side
+    int pc;                 // padded coefficient stride
+    int nchunk;             // K chunks per matrix
+    int *err;               // device error word
+};
+
+struct Ctx {
+    vfmm_config cfg;
+    cudaStream_t stream = nullptr;
+    int p = 10, nc = 121, pc = 128;
+    bool f64 = false;
+    size_t esz = 4;  // element size of T
+
+    // tree
+    int64_t n = 0;
+    int depth = 0, nside = 1;
+    int64_t nleaf = 1;
+    int max_leaf = 0;
+    int last_R = 0;
+    bool built = false;
+    double leaf_w = 0.0;
+
+    // device buffers
+    DevBuf xs, gs, perm, keys, leaf_start, counts, fill, tmpidx, scan_part, err, maxleaf;
+    DevBuf mexp, lexp;             // all levels, T
+    DevBuf mhi, mlo;               // tensor-core copies of the multipoles (largest level)
+    DevBuf ufar, sfar;             // far-field u, S in sorted order, T
+    DevBuf at_m2l, at_m2m, at_l2l; // CUDA-core matrices, T
+    DevBuf tc_hi, tc_lo;           // tensor-core tiles
+    DevBuf m2m_f64, lattice_f64;   // root accumulation and lattice operator, FP64
+    DevBuf root_m;                 // FP64 root multipole
+    DevBuf kblocks;                // k-block lists (device)
+    DevBuf hx, hg, hu, hs;         // staging for vfmm_eval_host
+    std::vector<size_t> lvl_off;   // element offset of each level in mexp / lexp
+
+    // k-block lists (offsets into kblocks)
+    int kb_m2l_off[3][8], kb_m2l_cnt[3][8];  // index = near rings R at that level (1 or 2)
+    int kb_m2m_off = 0, kb_l2l_off[8];
+
+    cudaEvent_t ev[10];
+    bool have_events = false;
+    bool timed_eval = false;
+    double timings[NPHASE];
+    std::string last_error;
+};
+
+// kernels.cu entry points (host launchers)
+int launch_tree(Ctx *c, const void *x);
+int launch_gather_gamma(Ctx *c, const void *gamma);
+int launch_p2m(Ctx *c);
+int launch_gemm(Ctx *c, const GemmParams &gp, int ngroups, int64_t ncell_group);
+int launch_root(Ctx *c);
+int launch_l2p(Ctx *c);
+int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, void *u_out,
+               void *s_out, int images_only_direct);
+int launch_tc_m2l(Ctx *c, int level, const int4 *kb_dev, const int *kb_off, const int *kb_cnt, bool bf16);
+int launch_split(Ctx *c, int level, bool bf16);
+void set_constants(int p);
+
+}  // namespace vfmm

@@ -1,0 +1,153 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Tolerances (derived in the design notes):
+* direct sum, FP64 kernels: 1e-12 relative L2 (only summation order and erf/exp rounding
+  differ);
+* direct sum, FP32 kernels: 2e-5 (FP32 accumulation of ~1e5 terms plus the 1.5e-7 error of
+  the Abramowitz-Stegun erf);
+* FMM at p = 10: u <= 1e-4 and S <= 1e-3 relative L2 (the accuracy target, 4 digits in the
+  paper's Section 4.1 performance paragraph).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload as wl
+from gpu_util import rel_l2, rel_l2_demeaned, run_fmm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def field16():
+    return wl.make_vortex_lattice(16, 4, 1)
+
+
+@pytest.fixture(scope="module")
+def oracle16_k1(field16):
+    f = field16
+    return oracle.direct(f["x"], f["alpha"], f["sigma"], K=1)
+
+
+def test_direct_fp64_matches_oracle(field16, oracle16_k1):
+    f = field16
+    u, s, _ = run_fmm(f["x"], f["alpha"], f["sigma"], method="direct", direct_images=1, dtype="f64")
+    uo, so = oracle16_k1
+    assert rel_l2(u, uo) < 1e-12
+    assert rel_l2(s, so) < 1e-12
+
+
+def test_direct_fp32_matches_oracle(field16, oracle16_k1):
+    f = field16
+    u, s, _ = run_fmm(f["x"], f["alpha"], f["sigma"], method="direct", direct_images=1, dtype="f32")
+    uo, so = oracle16_k1
+    assert rel_l2(u, uo) < 2e-5
+    assert rel_l2(s, so) < 2e-5
+
+
+def test_direct_jittered_ragged_and_coincident():
+    # non-lattice positions (ragged leaves), points outside [0, L) that must wrap, and two
+    # coincident distinct particles (their stretching pair term is the finite r -> 0 limit)
+    n = 7
+    h = 2 * np.pi / n
+    rng = np.random.default_rng(4)
+    x = wl.jitter(wl.lattice_positions(n), h, 0.45, seed=2)
+    x[5] += np.array([2 * np.pi, -2 * np.pi, 0.0])
+    x = np.vstack([x, x[10:11]])
+    g = rng.normal(size=x.shape)
+    sigma = 0.9 * h
+    xo = np.mod(x, 2 * np.pi)
+    uo, so = oracle.direct(xo, g, sigma, K=1)
+    u, s, _ = run_fmm(x, g, sigma, method="direct", direct_images=1, dtype="f64")
+    assert rel_l2(u, uo) < 1e-12
+    assert rel_l2(s, so) < 1e-12
+
+
+@pytest.mark.parametrize("p", [4, 6, 8, 10])
+def test_fmm_fp64_order_convergence(field16, oracle16_k1, p, request):
+    f = field16
+    u, s, info = run_fmm(f["x"], f["alpha"], f["sigma"], method="fmm", p=p, depth=2,
+                         periodic_levels=0, dtype="f64")
+    uo, so = oracle16_k1
+    eu, es = rel_l2(u, uo), rel_l2(s, so)
+    print("p=%d depth=%d R=%d: u %.3e S %.3e" % (p, info["depth"], info["near_rings"], eu, es))
+    bound_u = {4: 3e-2, 6: 3e-3, 8: 5e-4, 10: 1e-4}[p]
+    bound_s = {4: 1e-1, 6: 2e-2, 8: 5e-3, 10: 1e-3}[p]
+    assert eu < bound_u
+    assert es < bound_s
+
+
+def test_fmm_fp32_matches_fp64_fmm(field16):
+    f = field16
+    kw = dict(method="fmm", p=10, depth=2, periodic_levels=1)
+    u64, s64, _ = run_fmm(f["x"], f["alpha"], f["sigma"], dtype="f64", **kw)
+    u32, s32, _ = run_fmm(f["x"], f["alpha"], f["sigma"], dtype="f32", m2l="fp32", **kw)
+    assert rel_l2(u32, u64) < 2e-5
+    assert rel_l2(s32, s64) < 2e-5
+
+
+def test_fmm_periodic_one_super_level(field16):
+    f = field16
+    tid = wl.target_subset(4096, 512, seed=3)
+    uo, so = oracle.direct(f["x"], f["alpha"], f["sigma"], K=4, targets=tid)
+    u, s, _ = run_fmm(f["x"], f["alpha"], f["sigma"], method="fmm", p=10, depth=2,
+                      periodic_levels=1, dtype="f64")
+    assert rel_l2(u[tid], uo) < 1e-4
+    assert rel_l2(s[tid], so) < 1e-3
+
+
+def test_fmm_periodic_27cubed_images(field16):
+    # the paper's 3^3 x 3^3 x 3^3 image cube (S = 2, K = 13), on a seeded target subset
+    f = field16
+    tid = wl.target_subset(4096, 48, seed=3)
+    uo, so = oracle.direct(f["x"], f["alpha"], f["sigma"], K=13, targets=tid)
+    u, s, _ = run_fmm(f["x"], f["alpha"], f["sigma"], method="fmm", p=10, depth=2,
+                      periodic_levels=2, dtype="f32", m2l="fp32")
+    assert rel_l2(u[tid], uo) < 1e-4
+    assert rel_l2(s[tid], so) < 1e-3
+
+
+def test_fmm_64cubed_sampled_fp32():
+    f = wl.make_vortex_lattice(64, 8, 1)
+    tid = wl.target_subset(64 ** 3, 96, seed=3)
+    uo, so = oracle.direct(f["x"], f["alpha"], f["sigma"], K=1, targets=tid)
+    u, s, info = run_fmm(f["x"], f["alpha"], f["sigma"], method="fmm", p=10, periodic_levels=0,
+                         dtype="f32", m2l="fp32")
+    print(info, rel_l2(u[tid], uo), rel_l2(s[tid], so))
+    assert rel_l2(u[tid], uo) < 1e-4
+    assert rel_l2(s[tid], so) < 1e-3
+
+
+def test_fmm_jittered_nonuniform_leaves():
+    # random (not lattice) positions: empty and crowded leaves, ragged tails
+    n = 24
+    h = 2 * np.pi / n
+    rng = np.random.default_rng(9)
+    x = rng.uniform(0, 2 * np.pi, (n ** 3, 3))
+    g = rng.normal(size=x.shape) * h ** 3
+    g -= g.mean(0)
+    sigma = h
+    tid = wl.target_subset(len(x), 128, seed=5)
+    uo, so = oracle.direct(x, g, sigma, K=1, targets=tid)
+    u, s, info = run_fmm(x, g, sigma, method="fmm", p=10, depth=2, periodic_levels=0, dtype="f64")
+    assert info["max_leaf"] > 216
+    assert rel_l2(u[tid], uo) < 1e-4
+    assert rel_l2(s[tid], so) < 1e-3
+
+
+def test_errors_reported():
+    torch = pytest.importorskip("torch")
+    import paper_1110_2921_gb300 as vf
+    h = vf.VortexFMM(m2l="fp32")
+    try:
+        g = torch.zeros(8, 3, device="cuda")
+        with pytest.raises(vf.VfmmError) as e:
+            h.eval(g, 0.1)
+        assert e.value.status == -4
+        x = torch.rand(8, 3, device="cuda")
+        h.build_tree(x)
+        with pytest.raises(vf.VfmmError) as e:
+            h.eval(g, float("nan"))
+        assert e.value.status == -1
+    finally:
+        h.close()
