@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput of the periodic FMM evaluation of u and the stretching term.
+
+Workload (one "step" = the whole hot path once): 256^3 = 16,777,216 vortex particles on the
+cell-centre lattice of [0, 2 pi)^3, seeded random-phase solenoidal field with
+E(k) ~ k^4 exp(-2 k^2/k0^2), k0 = 4, unit energy, alpha = omega h^3, sigma = h; FMM order
+p = 10, 27^3 periodic images (3 super-levels of the image lattice, S = 2).  A step is
+vfmm_build_tree (wrap, Morton-free leaf keys, counting sort) + vfmm_eval_velocity_stretching
+(P2M, M2M, FP64 root and lattice operator, M2L, L2L, L2P, P2P + un-permute).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
+Multi-GPU (torchrun): every rank evaluates its own independent field (seed 1 + rank):
+replicas, weak scaling, no data-path collective.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s for u+stretching at 256³ (p=10), rel-L2 err vs FP64 direct sum"
+PAPER_PARTICLES_PER_S = 0.84e6   # 256^3 / 20 s per step at p=10 on one C2070 (paper, Section 4.1)
+FLOPS_PER_PAIR = 65              # FP32 operations of one P2P pair interaction (FMA = 2)
+MUFU_PER_PAIR = 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="vfmm", choices=["vfmm", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="particles per side")
+    ap.add_argument("--p", type=int, default=10)
+    ap.add_argument("--k0", type=int, default=4)
+    ap.add_argument("--m2l", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3"])
+    ap.add_argument("--periodic-levels", type=int, default=2)
+    ap.add_argument("--check", type=int, default=16, help="sampled targets for the oracle error (0 = off)")
+    ap.add_argument("--cpu-targets", type=int, default=0, help="oracle targets for cpu_baseline (0 = one per host core)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def leaf_pairs(x, L, depth, R):
+    """Source-target pairs the P2P visits: sum over leaves c of n_c * sum_{|t|<=R} n_{c+t}."""
+    import numpy as np
+    ns = 1 << depth
+    c = np.clip((np.mod(x, L) / L * ns).astype(np.int64), 0, ns - 1)
+    cnt = np.bincount((c[:, 0] * ns + c[:, 1]) * ns + c[:, 2], minlength=ns ** 3).reshape(ns, ns, ns)
+    cnt = cnt.astype(np.float64)
+    acc = np.zeros_like(cnt)
+    for dx in range(-R, R + 1):
+        for dy in range(-R, R + 1):
+            for dz in range(-R, R + 1):
+                acc += np.roll(cnt, (dx, dy, dz), axis=(0, 1, 2))
+    return float((cnt * acc).sum())
+
+
+def source_hash(*names):
+    h = hashlib.sha1()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_1110_2921_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kernel, src):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "counters.json")
+    try:
+        d = json.load(open(path))[kernel]
+    except Exception:
+        return None
+    if d.get("source_hash") != source_hash(*src):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def oracle_rate(f, targets, K):
+    """FP64 oracle (as it stands) on a target sample: seconds and threads used."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.direct(f["x"], f["alpha"], f["sigma"], K=K, targets=targets)
+    dt = time.perf_counter() - t0
+    return dt, os.cpu_count()
+
+
+def cpu_baseline(f, ntargets):
+    """Oracle particles/s for the workload's definition (27^3 image boxes), from a timed
+    sample of targets with the central 27 boxes; the 27^3-box cost is the same loop over
+    729 times as many (target, source, box) triples."""
+    import workload as wl
+    N = len(f["x"])
+    tid = wl.target_subset(N, ntargets, seed=11)
+    dt, cores = oracle_rate(f, tid, K=1)
+    cores = min(cores, ntargets)
+    boxes_full = (2 * 13 + 1) ** 3
+    value = ntargets / dt * 27.0 / boxes_full
+    sample = ("%d targets of the %d-particle field, direct FP64 sum over the central 27 image boxes in %.1f s; "
+              "scaled by 27/%d to the 27^3-box sum" % (ntargets, N, dt, boxes_full))
+    return {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle", "sample": sample,
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import workload as wl
+    n = args.n
+    f = wl.make_vortex_lattice(n, args.k0, 1)
+    nt = args.cpu_targets or os.cpu_count()
+    for _ in range(args.warmup):
+        cpu_baseline(f, nt)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        cb = cpu_baseline(f, nt)
+        vals.append(cb["value"])
+        secs += cb["seconds"]
+    value = len(vals) * nt / secs * 27.0 / (27 ** 3)
+    cb["value"] = value
+    cb["sample"] = "%d steps of %d targets each; " % (args.steps, nt) + cb["sample"].split("; ", 1)[0] + \
+        "; scaled by 27/19683 to the 27^3-box sum"
+    out = {"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": value / PAPER_PARTICLES_PER_S, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": "vortex lattice %d^3, k0=%d, sigma=h, 27^3 periodic images" % (n, args.k0),
+                      "n_particles": n ** 3, "direct_sum": "FP64 CPU oracle"},
+           "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import workload as wl
+    import paper_1110_2921_gb300 as vf
+    from paper_1110_2921_gb300 import build
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    n = args.n
+    N = n ** 3
+    f = wl.make_vortex_lattice(n, args.k0, 1 + rank)
+    sigma = f["sigma"]
+    X = torch.tensor(f["x"], dtype=torch.float32, device=dev)
+    G = torch.tensor(f["alpha"], dtype=torch.float32, device=dev)
+    U = torch.empty_like(G)
+    S = torch.empty_like(G)
+    h = vf.VortexFMM(p=args.p, periodic_levels=args.periodic_levels, m2l=args.m2l)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h.build_tree(X)
+        h.eval(G, sigma, out=(U, S))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = h.tree_info()
+    launches = info["launches"]
+    clocks = ClockSampler(dev.index) if rank == 0 else None
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    phase_ms = []
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+        h.sync()   # per-step phase timings are read from the library's own events
+        phase_ms.append(h.timings())
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = t0.elapsed_time(t1)
+    clk = clocks.stop() if clocks else None
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    value = ws * N * args.steps / (ms_max / 1e3)
+
+    # end to end from pinned host memory through vfmm_eval_host (H2D x, gamma; D2H u, S)
+    xh = torch.tensor(f["x"], dtype=torch.float32).pin_memory()
+    gh = torch.tensor(f["alpha"], dtype=torch.float32).pin_memory()
+    uh = torch.empty_like(gh).pin_memory()
+    sh = torch.empty_like(gh).pin_memory()
+    lib = vf._native
+    lib.vfmm_eval_host(h.h, N, xh.data_ptr(), gh.data_ptr(), sigma, uh.data_ptr(), sh.data_ptr())
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        lib.vfmm_eval_host(h.h, N, xh.data_ptr(), gh.data_ptr(), sigma, uh.data_ptr(), sh.data_ptr())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
+    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = ws * N / (float(e2e_t.item()) / 1e3)
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.barrier()
+        return
+
+    # roofline of the dominant kernel (P2P): FP32 ALU bound
+    p2p_ms = statistics.mean(p["p2p"] for p in phase_ms)
+    R = info["near_rings"]
+    pairs = leaf_pairs(f["x"], 2 * math.pi, info["depth"], R)
+    achieved = FLOPS_PER_PAIR * pairs / (p2p_ms / 1e3) / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak = 2 * 128 * sms * 2.070e9 / 1e12
+    traffic = profiled_traffic("k_p2p_f32", ["p2p.cu"])
+    phases = {k: round(statistics.mean(p[k] for p in phase_ms), 3) for k in phase_ms[0]}
+
+    out_err = {}
+    if args.check:
+        import oracle
+        tid = wl.target_subset(N, args.check, seed=3)
+        uo, so = oracle.direct(f["x"], f["alpha"], sigma, K=1, targets=tid)
+        h0 = vf.VortexFMM(p=args.p, periodic_levels=0, m2l=args.m2l)
+        h0.build_tree(X)
+        u0, s0 = h0.eval(G, sigma)
+        h0.sync()
+        u0 = u0.double().cpu().numpy()[tid]
+        s0 = s0.double().cpu().numpy()[tid]
+        h0.close()
+        out_err = {"rel_l2_u": float(np.linalg.norm(u0 - uo) / np.linalg.norm(uo)),
+                   "rel_l2_S": float(np.linalg.norm(s0 - so) / np.linalg.norm(so)),
+                   "targets": args.check, "images": "27 central boxes (same tree, S=0)"}
+
+    cb = cpu_baseline(f, args.cpu_targets or os.cpu_count()) if ws == 1 else None
+    h2d = 2 * N * 3 * 4
+    d2h = 2 * N * 3 * 4
+    out = {
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": value / PAPER_PARTICLES_PER_S, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "vortex lattice %d^3 (%d particles), k0=%d, sigma=h, p=%d, 27^3 periodic images"
+                   % (n, N, args.k0, args.p), "n_particles": N, "p": args.p, "m2l": args.m2l,
+                   "periodic_levels": args.periodic_levels, "depth": info["depth"], "near_rings": R,
+                   "l2": "inputs (x, gamma 402 MB) larger than L2; no flush",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_p2p_f32",
+                     "pairs_per_launch": pairs, "flops_per_pair": FLOPS_PER_PAIR,
+                     "peak_basis": "2 x 128 FP32 lanes x %d SMs x 2070 MHz" % sms},
+        "phases_ms": phases,
+        "accuracy": out_err,
+        "clocks": clk,
+        "cpu_baseline": cb,
+    }
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+
+
+if __name__ == "__main__":
+    main()

@@ -70,7 +70,7 @@ extern "C" {
 #define VFMM_METHOD_DIRECT 1 /* all pairs over the (2K+1)^3 image cube, K = direct_images */
 
 typedef struct vfmm_config {
-    int p;               /* expansion order: degrees 0..p, (p+1)^2 coefficients (Eq. fmm3dm); 2 <= p <= 16 */
+    int p;               /* expansion order: degrees 0..p, (p+1)^2 coefficients (Eq. fmm3dm); 2 <= p <= 10 */
     int depth;           /* leaf depth D of the uniform octree; 0 = choose from ncrit */
     int ncrit;           /* target mean particles per leaf when depth == 0 */
     int near_rings;      /* R: near field = (2R+1)^3 leaves; 0 = smallest R with R w >= rho_cut sigma; R <= 2 */
@@ -130,7 +130,8 @@ int vfmm_sync(vfmm_handle h);
 int vfmm_get_timings(vfmm_handle h, double *ms_per_phase, int nphase);
 
 /* Tree facts: out[0] = depth D, out[1] = near rings R used by the last evaluation,
- * out[2] = leaves per side, out[3] = maximum particles in one leaf, out[4] = particles. */
+ * out[2] = leaves per side, out[3] = maximum particles in one leaf, out[4] = particles,
+ * out[5] = CUDA kernels launched by the last vfmm_build_tree plus the evaluations since. */
 int vfmm_get_tree_info(vfmm_handle h, int64_t *out, int nout);
 
 /* Name of a status code (static string). */

@@ -62,6 +62,62 @@ template <typename T> std::vector<T> to_at(const std::vector<double> &A, int nc,
     return AT;
 }
 
+// Round-to-nearest-even float -> bfloat16 bits (finite inputs).
+inline uint16_t bf16_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+inline float bf16_value(uint16_t h)
+{
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+// Round to the TF32 grid (10 explicit mantissa bits, ties away from zero), kept as float.
+inline float tf32_value(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u = (u + 0x1000u) & ~0x1FFFu;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+// Tensor-core operand tiles: for each matrix and each 64-byte K chunk, the 128 x 64 B tile in
+// the canonical no-swizzle K-major layout: byte (k/8)*512 + kgroup*128 + (k%8)*16 + (byte in group).
+void tile_matrix(const std::vector<double> &A, int nc, int pc, bool bf16, unsigned char *hi, unsigned char *lo)
+{
+    const int esz = bf16 ? 2 : 4;
+    const int kc = 64 / esz;
+    const int nchunk = pc / kc;
+    for (int ch = 0; ch < nchunk; ++ch) {
+        unsigned char *th = hi + (size_t)ch * 8192, *tl = lo + (size_t)ch * 8192;
+        for (int k = 0; k < 128; ++k)
+            for (int e = 0; e < kc; ++e) {
+                int j = ch * kc + e;
+                double a = (k < nc && j < nc) ? A[(size_t)k * nc + j] : 0.0;
+                size_t byte = (size_t)(k / 8) * 512 + (size_t)((e * esz) / 16) * 128 + (size_t)(k % 8) * 16 +
+                              (size_t)((e * esz) % 16);
+                if (bf16) {
+                    uint16_t h = bf16_bits((float)a);
+                    uint16_t l = bf16_bits((float)(a - (double)bf16_value(h)));
+                    std::memcpy(th + byte, &h, 2);
+                    std::memcpy(tl + byte, &l, 2);
+                } else {
+                    float h = tf32_value((float)a);
+                    float l = tf32_value((float)(a - (double)h));
+                    std::memcpy(th + byte, &h, 4);
+                    std::memcpy(tl + byte, &l, 4);
+                }
+            }
+    }
+}
+
 inline int tindex(int tx, int ty, int tz) { return ((tx + 3) * 7 + (ty + 3)) * 7 + (tz + 3); }
 
 template <typename T> int upload_vec(Ctx *c, DevBuf &b, const std::vector<T> &v, const char *what)
@@ -78,13 +134,24 @@ template <typename T> int build_operators(Ctx *c)
     const int p = c->p, nc = c->nc, pc = c->pc;
     // M2L: k-block offset t (source = target + t) uses the operator of d = target - source = -t
     std::vector<T> m2l((size_t)NT * pc * OUT_ROWS, T(0));
+    const bool tc = c->cfg.m2l_prec == VFMM_M2L_TF32X3 || c->cfg.m2l_prec == VFMM_M2L_BF16X3;
+    const bool bf16 = c->cfg.m2l_prec == VFMM_M2L_BF16X3;
+    const size_t tile_bytes = (size_t)pc * (bf16 ? 2 : 4) / 64 * 8192;  // all K chunks of one matrix
+    std::vector<unsigned char> thi, tlo;
+    if (tc) {
+        thi.assign((size_t)NT * tile_bytes, 0);
+        tlo.assign((size_t)NT * tile_bytes, 0);
+    }
     for (int tx = -3; tx <= 3; ++tx)
         for (int ty = -3; ty <= 3; ++ty)
             for (int tz = -3; tz <= 3; ++tz) {
                 if (std::abs(tx) <= 1 && std::abs(ty) <= 1 && std::abs(tz) <= 1) continue;
                 double d[3] = {-(double)tx, -(double)ty, -(double)tz};
-                std::vector<T> at = to_at<T>(ops::m2l_hat(d, p), nc, pc);
-                std::copy(at.begin(), at.end(), m2l.begin() + (size_t)tindex(tx, ty, tz) * pc * OUT_ROWS);
+                std::vector<double> A = ops::m2l_hat(d, p);
+                std::vector<T> at = to_at<T>(A, nc, pc);
+                int ti = tindex(tx, ty, tz);
+                std::copy(at.begin(), at.end(), m2l.begin() + (size_t)ti * pc * OUT_ROWS);
+                if (tc) tile_matrix(A, nc, pc, bf16, thi.data() + ti * tile_bytes, tlo.data() + ti * tile_bytes);
             }
     std::vector<T> m2m((size_t)8 * pc * OUT_ROWS), l2l((size_t)8 * pc * OUT_ROWS);
     std::vector<double> m2m64((size_t)8 * nc * nc);
@@ -102,6 +169,10 @@ template <typename T> int build_operators(Ctx *c)
     std::vector<double> lat = ops::lattice_operator(p, c->cfg.periodic_levels);
     int st;
     if ((st = upload_vec(c, c->at_m2l, m2l, "M2L operators"))) return st;
+    if (tc) {
+        if ((st = upload_vec(c, c->tc_hi, thi, "tensor-core M2L tiles"))) return st;
+        if ((st = upload_vec(c, c->tc_lo, tlo, "tensor-core M2L tiles"))) return st;
+    }
     if ((st = upload_vec(c, c->at_m2m, m2m, "M2M operators"))) return st;
     if ((st = upload_vec(c, c->at_l2l, l2l, "L2L operators"))) return st;
     if ((st = upload_vec(c, c->m2m_f64, m2m64, "FP64 M2M operators"))) return st;
@@ -311,8 +382,15 @@ int build_impl(Ctx *c, int64_t n, const void *x)
         if ((st = ensure(c, c->mexp, tot * esz, "multipoles"))) return st;
         if ((st = ensure(c, c->lexp, tot * esz, "locals"))) return st;
         if ((st = ensure(c, c->ufar, (size_t)n * 3 * esz, "far velocity"))) return st;
+        if (c->cfg.m2l_prec == VFMM_M2L_TF32X3 || c->cfg.m2l_prec == VFMM_M2L_BF16X3) {
+            size_t cnt = ((size_t)1 << (3 * D)) * 3 * c->pc;
+            size_t eb = c->cfg.m2l_prec == VFMM_M2L_BF16X3 ? 2 : 4;
+            if ((st = ensure(c, c->mhi, cnt * eb, "multipole hi"))) return st;
+            if ((st = ensure(c, c->mlo, cnt * eb, "multipole lo"))) return st;
+        }
         if ((st = ensure(c, c->sfar, (size_t)n * 3 * esz, "far stretching"))) return st;
     }
+    c->launches = 0;
     cudaEventRecord(c->ev[0], c->stream);
     if ((st = launch_tree(c, x))) return st;
     cudaEventRecord(c->ev[1], c->stream);
@@ -496,8 +574,8 @@ int vfmm_get_tree_info(vfmm_handle h, int64_t *out, int nout)
 {
     if (!h || !out) return VFMM_ERR_ARG;
     Ctx *c = &h->c;
-    int64_t v[5] = {c->depth, c->last_R, c->nside, c->max_leaf, c->n};
-    for (int i = 0; i < nout && i < 5; ++i) out[i] = v[i];
+    int64_t v[6] = {c->depth, c->last_R, c->nside, c->max_leaf, c->n, c->launches};
+    for (int i = 0; i < nout && i < 6; ++i) out[i] = v[i];
     return VFMM_OK;
 }
 

@@ -40,6 +40,7 @@ __device__ __forceinline__ int floordiv_pow2(int v, int log2n) { return v >> log
 
 #define VFMM_CUDA_CHECK_LAUNCH(ctx)                                                       \
     do {                                                                                  \
+        (ctx)->launches++;                                                                \
         cudaError_t e_ = cudaGetLastError();                                              \
         if (e_ != cudaSuccess) {                                                          \
             (ctx)->last_error = std::string("kernel launch: ") + cudaGetErrorString(e_);  \

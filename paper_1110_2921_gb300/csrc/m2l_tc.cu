@@ -1,19 +1,364 @@
-// Tensor-core M2L (placeholder until the tcgen05 kernel lands).
+// M2L on the fifth-generation tensor cores (tcgen05, TMEM accumulators).
+//
+// For target cells c of one parity g at level l and each offset t of their interaction list
+// (children of the parent's neighbours outside the near field; Section 3.1 uses M2L between
+// well-separated cells), L_c += T_t M_{(c + t) mod 2^l}: every cell pair that shares a lattice
+// offset shares the translation matrix, so the whole list is one implicit GEMM
+//   D[128 out coefs][64 cells x 3 components] = sum_t sum_j A_t[k][j] B_t[n][j]
+// with A_t the (pre-tiled) translation matrix and B_t the gathered multipole rows.
+//
+// Precision: inputs are split x = hi + lo (hi, lo both BF16, or both TF32) and three products
+// hi*hi + hi*lo + lo*hi are accumulated in FP32 in TMEM; the dropped lo*lo term is ~2^-16
+// (BF16) or ~2^-22 (TF32) relative.
+//
+// Mechanics (sm_103a): 128 threads; one elected thread issues tcgen05.mma (M = 128,
+// N = 192, K = 16 bf16 / 8 tf32 per instruction) from shared-memory descriptors in the
+// canonical no-swizzle K-major layout (8-row x 16-byte core matrices; K-adjacent core
+// matrices 128 B apart, 8-row groups 512 B apart); operands stream through a 4-stage
+// cp.async pipeline; tcgen05.commit arrives on one mbarrier per stage so a stage is refilled
+// only after the MMAs that read it completed.  Every mbarrier wait is bounded: on timeout
+// the kernel sets an error bit, waits (bounded) for its own loads, frees TMEM and returns.
 #include "common.cuh"
 #include "vfmm_internal.h"
 
+#include <cuda_bf16.h>
+
 namespace vfmm {
 
-int launch_split(Ctx *c, int, bool)
+constexpr int TC_THREADS = 128;
+constexpr int TC_CELLS = 64;
+constexpr int TC_N = 3 * TC_CELLS;          // 192 columns
+constexpr int TC_M = 128;
+constexpr int TC_STAGES = 4;
+constexpr int TC_KBYTES = 64;               // K bytes per stage per row
+constexpr int TC_A_BYTES = TC_M * TC_KBYTES;     // 8 KB
+constexpr int TC_B_BYTES = TC_N * TC_KBYTES;     // 12 KB
+constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 40 KB
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 2048;       // + alignment, barriers, tmem slot
+constexpr int TC_TMEM_COLS = 256;
+constexpr long long TC_WAIT_LIMIT = 1LL << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
-    c->last_error = "tensor-core M2L not built";
-    return VFMM_ERR_UNSUPPORTED;
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    // base offset 0, relative LBO, layout type 0 = no swizzle
+    return d;
 }
 
-int launch_tc_m2l(Ctx *c, int, const int4 *, const int *, const int *, bool)
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
-    c->last_error = "tensor-core M2L not built";
-    return VFMM_ERR_UNSUPPORTED;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <bool BF16>
+__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    if (BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcParams tp)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-align the stage area
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *stages = base;
+    uint64_t *bars = (uint64_t *)(base + TC_STAGES * TC_STAGE_BYTES);
+    uint32_t *tmem_slot = (uint32_t *)(bars + TC_STAGES);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = blockIdx.y;
+    const int n = tp.n, half = n >> 1;
+    const int64_t cell0 = (int64_t)blockIdx.x * TC_CELLS;
+    const int nkb = tp.kb_cnt[g];
+    const int4 *kbl = tp.kb + tp.kb_off[g];
+    const int nchunk = tp.nchunk;
+    const int nk = nkb * nchunk;
+    const int pc = tp.pc;
+    const int esz = BF16 ? 2 : 4;
+
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+
+    // per-thread B slots: chunk v = tid + 128 j, row nrow = 8 (v >> 5) + (v & 7), k-group (v >> 3) & 3
+    int slot_cx[6], slot_cy[6], slot_cz[6], slot_comp[6], slot_kg[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        int v = tid + TC_THREADS * j;
+        int nrow = 8 * (v >> 5) + (v & 7);
+        slot_kg[j] = (v >> 3) & 3;
+        int q = nrow / 3;
+        slot_comp[j] = nrow - 3 * q;
+        int64_t P = cell0 + q;
+        int px = (int)(P / ((int64_t)half * half)), py = (int)((P / half) % half), pz = (int)(P % half);
+        slot_cx[j] = 2 * px + ((g >> 2) & 1);
+        slot_cy[j] = 2 * py + ((g >> 1) & 1);
+        slot_cz[j] = 2 * pz + (g & 1);
+    }
+    const unsigned char *Ahi = (const unsigned char *)tp.Ahi, *Alo = (const unsigned char *)tp.Alo;
+    const unsigned char *Bhi = (const unsigned char *)tp.Bhi, *Blo = (const unsigned char *)tp.Blo;
+    const size_t row_bytes = (size_t)pc * esz;
+
+    auto load_stage = [&](int i) {
+        int kbi = i / nchunk, ch = i - kbi * nchunk;
+        int4 kb = kbl[kbi];
+        unsigned char *st = stages + (i % TC_STAGES) * TC_STAGE_BYTES;
+        uint32_t sA = smem_u32(st), sAl = sA + TC_A_BYTES, sB = sAl + TC_A_BYTES, sBl = sB + TC_B_BYTES;
+        const unsigned char *ah = Ahi + ((size_t)kb.x * nchunk + ch) * TC_A_BYTES;
+        const unsigned char *al = Alo + ((size_t)kb.x * nchunk + ch) * TC_A_BYTES;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int v = tid + TC_THREADS * j;  // 512 chunks of 16 B
+            cp_async16(sA + 16 * v, ah + 16 * v);
+            cp_async16(sAl + 16 * v, al + 16 * v);
+        }
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            int v = tid + TC_THREADS * j;
+            int sx = (slot_cx[j] + kb.y) & (n - 1);
+            int sy = (slot_cy[j] + kb.z) & (n - 1);
+            int sz = (slot_cz[j] + kb.w) & (n - 1);
+            int64_t src = ((int64_t)sx * n + sy) * n + sz;
+            size_t off = (size_t)(src * 3 + slot_comp[j]) * row_bytes + (size_t)ch * TC_KBYTES + 16 * slot_kg[j];
+            cp_async16(sB + 16 * v, Bhi + off);
+            cp_async16(sBl + 16 * v, Blo + off);
+        }
+    };
+
+    // instruction descriptor: D f32, A/B bf16 (1) or tf32 (2), K-major, N = 192, M = 128
+    const uint32_t fmt = BF16 ? 1u : 2u;
+    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                           ((uint32_t)(TC_M >> 4) << 24);
+    bool ok = true;
+
+    // prologue
+#pragma unroll
+    for (int i = 0; i < TC_STAGES - 1; ++i) {
+        if (i < nk) load_stage(i);
+        cp_async_commit();
+    }
+    for (int i = 0; i < nk; ++i) {
+        const int s = i % TC_STAGES;
+        const int ip = i + TC_STAGES - 1;
+        if (ip < nk) {
+            if (i >= 1) {
+                int pi = i - 1;
+                ok = mbar_wait(smem_u32(&bars[pi % TC_STAGES]), (uint32_t)((pi / TC_STAGES) & 1));
+            }
+        }
+        // a bounded wait that gave up anywhere ends the loop in every thread
+        if (!__syncthreads_and(ok ? 1 : 0)) {
+            ok = false;
+            break;
+        }
+        if (ip < nk) {
+            load_stage(ip);
+        }
+        cp_async_commit();
+        cp_async_wait<TC_STAGES - 1>();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            unsigned char *st = stages + s * TC_STAGE_BYTES;
+            uint32_t sA = smem_u32(st), sAl = sA + TC_A_BYTES, sB = sAl + TC_A_BYTES, sBl = sB + TC_B_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                uint32_t koff = 256u * ks;  // two 16-byte k-groups per MMA
+                uint64_t dAh = make_desc(sA + koff, 128, 512), dAl = make_desc(sAl + koff, 128, 512);
+                uint64_t dBh = make_desc(sB + koff, 128, 512), dBl = make_desc(sBl + koff, 128, 512);
+                uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
+                mma_issue<BF16>(tmem, dAh, dBh, idesc, acc0);
+                mma_issue<BF16>(tmem, dAh, dBl, idesc, 1u);
+                mma_issue<BF16>(tmem, dAl, dBh, idesc, 1u);
+            }
+            mma_commit(smem_u32(&bars[s]));
+        }
+    }
+    // all threads agree on ok (a failed wait is seen by every thread on the same barrier)
+    if (ok && nk > 0) {
+        int li = nk - 1;
+        ok = mbar_wait(smem_u32(&bars[li % TC_STAGES]), (uint32_t)((li / TC_STAGES) & 1));
+    }
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        // epilogue: warp w owns TMEM lanes 32w..32w+31 = output coefficients
+        const int k = 32 * warp + (tid & 31);
+        float *C = tp.C;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+            uint32_t r[16];
+            uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                int col = c0 + e;
+                int q = col / 3, comp = col - 3 * q;
+                int64_t P = cell0 + q;
+                int px = (int)(P / ((int64_t)half * half)), py = (int)((P / half) % half), pz = (int)(P % half);
+                int cx = 2 * px + ((g >> 2) & 1), cy = 2 * py + ((g >> 1) & 1), cz = 2 * pz + (g & 1);
+                int64_t cell = ((int64_t)cx * n + cy) * n + cz;
+                if (k < pc) C[(cell * 3 + comp) * pc + k] = __uint_as_float(r[e]);
+            }
+        }
+    } else {
+        if (tid == 0) atomicOr(tp.err, ERRBIT_TIMEOUT);
+        cp_async_wait<0>();  // this thread's copies in flight
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+    }
+}
+
+// FP32 multipoles -> hi/lo split in BF16 or TF32 (the latter kept in FP32 containers).
+__global__ void k_split_bf16(int64_t count, const float *__restrict__ M, __nv_bfloat16 *__restrict__ hi,
+                             __nv_bfloat16 *__restrict__ lo)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float v = M[i];
+    __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__device__ __forceinline__ float to_tf32(float v)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+__global__ void k_split_tf32(int64_t count, const float *__restrict__ M, float *__restrict__ hi, float *__restrict__ lo)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float v = M[i];
+    float h = to_tf32(v);
+    hi[i] = h;
+    lo[i] = to_tf32(v - h);
+}
+
+int launch_split(Ctx *c, int level, bool bf16)
+{
+    int64_t count = ((int64_t)1 << (3 * level)) * 3 * c->pc;
+    const float *M = (const float *)c->mexp.p + c->lvl_off[level];
+    int nb = (int)((count + 255) / 256);
+    if (bf16)
+        k_split_bf16<<<nb, 256, 0, c->stream>>>(count, M, (__nv_bfloat16 *)c->mhi.p, (__nv_bfloat16 *)c->mlo.p);
+    else
+        k_split_tf32<<<nb, 256, 0, c->stream>>>(count, M, (float *)c->mhi.p, (float *)c->mlo.p);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+int launch_tc_m2l(Ctx *c, int level, const int4 *kb_dev, const int *kb_off, const int *kb_cnt, bool bf16)
+{
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[bf16 ? 1 : 0]) {
+        cudaError_t e = bf16 ? cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)
+                             : cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        if (e != cudaSuccess) {
+            c->last_error = std::string("tensor-core M2L shared memory: ") + cudaGetErrorString(e);
+            return VFMM_ERR_CUDA;
+        }
+        attr_set[bf16 ? 1 : 0] = true;
+    }
+    const int n = 1 << level;
+    const int64_t ncg = (int64_t)(n / 2) * (n / 2) * (n / 2);
+    if (ncg % TC_CELLS != 0 || c->pc != TC_M) {
+        c->last_error = "tensor-core M2L needs 64 | (n/2)^3 and 128 padded coefficients";
+        return VFMM_ERR_UNSUPPORTED;
+    }
+    TcParams tp;
+    tp.Ahi = c->tc_hi.p;
+    tp.Alo = c->tc_lo.p;
+    tp.Bhi = c->mhi.p;
+    tp.Blo = c->mlo.p;
+    tp.C = (float *)c->lexp.p + c->lvl_off[level];
+    tp.kb = kb_dev;
+    for (int g = 0; g < 8; ++g) {
+        tp.kb_off[g] = kb_off[g];
+        tp.kb_cnt[g] = kb_cnt[g];
+    }
+    tp.n = n;
+    tp.pc = c->pc;
+    tp.nchunk = c->pc * (bf16 ? 2 : 4) / TC_KBYTES;
+    tp.err = (int *)c->err.p;
+    dim3 grid((unsigned)(ncg / TC_CELLS), 8);
+    if (bf16)
+        k_m2l_tc<true><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(tp);
+    else
+        k_m2l_tc<false><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(tp);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
 }
 
 }  // namespace vfmm

@@ -183,6 +183,7 @@ template <typename TIn, typename T> static int tree_impl(Ctx *c, const TIn *x)
     k_leaf_sort<TIn, T><<<(unsigned)nleaf, 256, 0, st>>>(start, (int *)c->tmpidx.p, x, c->cfg.box,
                                                          (int *)c->perm.p,
                                                          (typename V4<T>::type *)c->xs.p, (int *)c->err.p);
+    c->launches += 5;  // k_keys, three scan kernels and k_scatter precede k_leaf_sort
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
 }

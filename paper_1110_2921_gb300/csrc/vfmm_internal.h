@@ -101,6 +101,7 @@ struct Ctx {
     cudaEvent_t ev[10];
     bool have_events = false;
     bool timed_eval = false;
+    int64_t launches = 0;      // kernels launched by the last build + evaluation
     double timings[NPHASE];
     std::string last_error;
 };
