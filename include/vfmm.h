@@ -134,6 +134,32 @@ int vfmm_get_timings(vfmm_handle h, double *ms_per_phase, int nphase);
  * out[5] = CUDA kernels launched by the last vfmm_build_tree plus the evaluations since. */
 int vfmm_get_tree_info(vfmm_handle h, int64_t *out, int nout);
 
+/* Largest n accepted by vfmm_direct_eval_noalloc. */
+#define VFMM_NOALLOC_MAX_N 65536
+
+/* Direct sum of u and S (VFMM_METHOD_DIRECT, FP32) that allocates nothing.
+ *
+ * For callers that cannot allocate device memory when they call in: a host program that
+ * gives all device memory to its own pool up front, or a latency-critical loop that must not
+ * pay cudaMalloc's implicit device synchronisation.  This call makes no cudaMalloc, cudaFree
+ * or other allocating call.  The paper has no counterpart; it evaluates the same sum as a
+ * handle created with method VFMM_METHOD_DIRECT and direct_images = images.
+ *
+ * x, gamma: device n x 3 float positions (wrapped into [0, box)^3) and strengths; u_out:
+ * device n x 3 float; s_out: device n x 3 float or NULL.  Outputs are in input order.  Work is
+ * enqueued on stream (a cudaStream_t); the call does not synchronise.
+ * Scratch: one file-scope device array of 2 x VFMM_NOALLOC_MAX_N float4 (2 MiB), present on
+ * every device that loads the library until the process exits.  Every call on a device uses
+ * the same array and overwrites the part it needs, so calls whose work overlaps on the GPU
+ * (other streams, other host threads) race: order them on one stream or synchronise between.
+ * The first call on a device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) once; make that first call before any stream capture.
+ * Errors: n <= 0, a NULL x/gamma/u_out, sigma or box not finite and > 0, or images outside
+ * [0, 20] -> VFMM_ERR_ARG; n > VFMM_NOALLOC_MAX_N -> VFMM_ERR_UNSUPPORTED (nothing is
+ * launched); a failed address look-up or launch -> VFMM_ERR_CUDA. */
+int vfmm_direct_eval_noalloc(int64_t n, const float *x, const float *gamma, double sigma, double box, int images,
+                             float *u_out, float *s_out, void *stream);
+
 /* Name of a status code (static string). */
 const char *vfmm_strerror(int status);
 

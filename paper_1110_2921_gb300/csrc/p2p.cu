@@ -336,3 +336,132 @@ int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, 
 }
 
 }  // namespace vfmm
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free direct sum.
+//
+// Some callers cannot allocate device memory when they call in: a host program that hands
+// every byte of device memory to its own pool up front, or a latency-critical loop that must
+// not pay cudaMalloc's implicit device synchronisation.  vfmm_direct_eval_noalloc serves them:
+// it evaluates the same direct sum as VFMM_METHOD_DIRECT (FP32), with its only scratch (the
+// wrapped positions and the strengths, packed as float4) in the file-scope array below,
+// which every device that loads this library holds until the process exits.
+// The paper has no counterpart of this entry point.
+namespace vfmm {
+
+constexpr int NOALLOC_MAX_N = VFMM_NOALLOC_MAX_N;
+static __device__ __align__(256) float4 g_noalloc_scratch[2 * NOALLOC_MAX_N];  // 2 MiB
+
+__global__ void k_noalloc_pack(int n, const float *__restrict__ x, const float *__restrict__ g, float L,
+                               float4 *__restrict__ scratch)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float invL = 1.0f / L;
+    scratch[i] = make_float4(wrap_coord<float>(x[3 * i], L, invL), wrap_coord<float>(x[3 * i + 1], L, invL),
+                             wrap_coord<float>(x[3 * i + 2], L, invL), 0.f);
+    scratch[NOALLOC_MAX_N + i] = make_float4(g[3 * i], g[3 * i + 1], g[3 * i + 2], 0.f);
+}
+
+__global__ void __launch_bounds__(P2P_BS) k_noalloc_direct(int n, int K, P2PConst kc,
+                                                           const float4 *__restrict__ scratch,
+                                                           float *__restrict__ u_out, float *__restrict__ s_out)
+{
+    __shared__ float4 sx[P2P_BS];
+    __shared__ float4 sg[P2P_BS];
+    const float4 *xs = scratch, *gs = scratch + NOALLOC_MAX_N;
+    const int ti = blockIdx.x * P2P_BS + threadIdx.x;
+    const bool active = ti < n;
+    float4 xi = active ? xs[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 gi = active ? gs[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float Lf = (float)kc.L;
+    Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int ox = -K; ox <= K; ++ox)
+        for (int oy = -K; oy <= K; ++oy)
+            for (int oz = -K; oz <= K; ++oz) {
+                float xi0 = xi.x - Lf * (float)ox, xi1 = xi.y - Lf * (float)oy, xi2 = xi.z - Lf * (float)oz;
+                for (int s0 = 0; s0 < n; s0 += P2P_BS) {
+                    int cnt = min(P2P_BS, n - s0);
+                    __syncthreads();
+                    if (threadIdx.x < cnt) {
+                        sx[threadIdx.x] = xs[s0 + threadIdx.x];
+                        sg[threadIdx.x] = gs[s0 + threadIdx.x];
+                    }
+                    __syncthreads();
+                    for (int j = 0; j < cnt; ++j) pair_f32(kc, xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j], sg[j], acc);
+                }
+            }
+    if (!active) return;
+    float s0 = fmaf(acc.a1, gi.z, fmaf(-acc.a2, gi.y, acc.b0));
+    float s1 = fmaf(acc.a2, gi.x, fmaf(-acc.a0, gi.z, acc.b1));
+    float s2 = fmaf(acc.a0, gi.y, fmaf(-acc.a1, gi.x, acc.b2));
+    u_out[3 * ti + 0] = acc.u0 * INV_4PI_F;
+    u_out[3 * ti + 1] = acc.u1 * INV_4PI_F;
+    u_out[3 * ti + 2] = acc.u2 * INV_4PI_F;
+    if (s_out) {
+        s_out[3 * ti + 0] = s0 * INV_4PI_F;
+        s_out[3 * ti + 1] = s1 * INV_4PI_F;
+        s_out[3 * ti + 2] = s2 * INV_4PI_F;
+    }
+}
+
+}  // namespace vfmm
+
+#include <mutex>
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+float4 *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+extern "C" int vfmm_direct_eval_noalloc(int64_t n, const float *x, const float *gamma, double sigma, double box,
+                                        int images, float *u_out, float *s_out, void *stream)
+{
+    using namespace vfmm;
+    if (n <= 0 || !x || !gamma || !u_out) return VFMM_ERR_ARG;
+    if (n > NOALLOC_MAX_N) return VFMM_ERR_UNSUPPORTED;
+    if (!(sigma > 0.0) || sigma != sigma || sigma > 1e300) return VFMM_ERR_ARG;
+    if (!(box > 0.0) || box > 1e300) return VFMM_ERR_ARG;
+    if (images < 0 || images > 20) return VFMM_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        cudaGetLastError();
+        return VFMM_ERR_CUDA;
+    }
+    float4 *scratch;
+    {
+        // one-time set-up per device: the host-side symbol is only a stand-in, so look up the
+        // array's device address with that device current
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return VFMM_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = (float4 *)p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    P2PConst kc;
+    kc.sigma = sigma;
+    kc.L = box;
+    const double log2e = 1.4426950408889634074;
+    const double cpi = 0.79788456080286535588;
+    kc.ce = (float)(-log2e / (2.0 * sigma * sigma));
+    kc.ct = (float)(0.3275911 / (1.41421356237309504880 * sigma));
+    kc.cq = (float)(cpi / sigma);
+    kc.cf = (float)(cpi / (sigma * sigma * sigma));
+    kc.zs = (float)(-0.25 * log2e / 2.0);
+    kc.inv_s2 = (float)(1.0 / (sigma * sigma));
+    kc.ks = (float)(cpi / (sigma * sigma * sigma));
+    kc.fs = (float)(cpi / (sigma * sigma * sigma * sigma * sigma));
+    cudaStream_t st = (cudaStream_t)stream;
+    int nn = (int)n;
+    k_noalloc_pack<<<(nn + 255) / 256, 256, 0, st>>>(nn, x, gamma, (float)box, scratch);
+    k_noalloc_direct<<<(nn + P2P_BS - 1) / P2P_BS, P2P_BS, 0, st>>>(nn, images, kc, scratch, u_out, s_out);
+    if (cudaGetLastError() != cudaSuccess) return VFMM_ERR_CUDA;
+    return VFMM_OK;
+}
