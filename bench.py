@@ -28,8 +28,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particles/s for u+stretching at 256³ (p=10), rel-L2 err vs FP64 direct sum"
 PAPER_PARTICLES_PER_S = 0.84e6   # 256^3 / 20 s per step at p=10 on one C2070 (paper, Section 4.1)
-FLOPS_PER_PAIR = 65              # FP32 operations of one P2P pair interaction (FMA = 2)
-MUFU_PER_PAIR = 3
+FLOPS_PER_PAIR = 65              # FP32 operations of one smoothed P2P pair (FMA = 2), + 3 MUFU
+FLOPS_PER_PAIR_SINGULAR = 45     # a pair of leaves >= 6.5 sigma apart (singular kernel), + 1 MUFU
 
 
 def parse():
@@ -104,19 +104,49 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def leaf_pairs(x, L, depth, R):
-    """Source-target pairs the P2P visits: sum over leaves c of n_c * sum_{|t|<=R} n_{c+t}."""
+def p2p_work(x, L, depth, R, sigma):
+    """Pairs the P2P visits, split as the kernel splits them by leaf-box separation d:
+    d < 6.5 sigma -> smoothed kernel (65 flops), d >= 6.5 sigma -> singular kernel (45 flops).
+    Returns (pairs, flops)."""
+    import itertools
     import numpy as np
     ns = 1 << depth
-    c = np.clip((np.mod(x, L) / L * ns).astype(np.int64), 0, ns - 1)
-    cnt = np.bincount((c[:, 0] * ns + c[:, 1]) * ns + c[:, 2], minlength=ns ** 3).reshape(ns, ns, ns)
-    cnt = cnt.astype(np.float64)
-    acc = np.zeros_like(cnt)
-    for dx in range(-R, R + 1):
-        for dy in range(-R, R + 1):
-            for dz in range(-R, R + 1):
-                acc += np.roll(cnt, (dx, dy, dz), axis=(0, 1, 2))
-    return float((cnt * acc).sum())
+    xf = np.mod(x, L).astype(np.float32).astype(np.float64)
+    c = np.clip((xf / L * ns).astype(np.int64), 0, ns - 1)
+    key = (c[:, 0] * ns + c[:, 1]) * ns + c[:, 2]
+    nleaf = ns ** 3
+    cnt = np.bincount(key, minlength=nleaf).astype(np.float64)
+    lo = np.full((nleaf, 3), 3e38)
+    hi = np.full((nleaf, 3), -3e38)
+    order = np.argsort(key, kind="stable")
+    xs = xf[order]
+    ne = cnt > 0
+    starts = np.concatenate([[0], np.cumsum(cnt)[:-1]]).astype(np.int64)[ne]
+    lo[ne] = np.minimum.reduceat(xs, starts, axis=0)
+    hi[ne] = np.maximum.reduceat(xs, starts, axis=0)
+    cnt = cnt.reshape(ns, ns, ns)
+    lo = lo.reshape(ns, ns, ns, 3)
+    hi = hi.reshape(ns, ns, ns, 3)
+    g = np.arange(ns)
+    C = np.meshgrid(g, g, g, indexing="ij")
+    d2_sing = 42.25 * sigma * sigma
+    p_s, p_g = 0.0, 0.0
+    for t in itertools.product(range(-R, R + 1), repeat=3):
+        nb = [C[d] + t[d] for d in range(3)]
+        sh = [np.floor_divide(nb[d], ns) * L for d in range(3)]
+        ix = [np.mod(nb[d], ns) for d in range(3)]
+        cn = cnt[ix[0], ix[1], ix[2]]
+        d2 = np.zeros_like(cnt)
+        for d in range(3):
+            slo = lo[ix[0], ix[1], ix[2], d] + sh[d]
+            shi = hi[ix[0], ix[1], ix[2], d] + sh[d]
+            gap = np.maximum(0.0, np.maximum(slo - hi[..., d], lo[..., d] - shi))
+            d2 += gap * gap
+        pairs = cnt * cn
+        sing = d2 >= d2_sing
+        p_g += float(pairs[sing].sum())
+        p_s += float(pairs[~sing].sum())
+    return p_s + p_g, FLOPS_PER_PAIR * p_s + FLOPS_PER_PAIR_SINGULAR * p_g
 
 
 def source_hash(*names):
@@ -288,8 +318,8 @@ def main():
     # roofline of the dominant kernel (P2P): FP32 ALU bound
     p2p_ms = statistics.mean(p["p2p"] for p in phase_ms)
     R = info["near_rings"]
-    pairs = leaf_pairs(f["x"], 2 * math.pi, info["depth"], R)
-    achieved = FLOPS_PER_PAIR * pairs / (p2p_ms / 1e3) / 1e12
+    pairs, flops = p2p_work(f["x"], 2 * math.pi, info["depth"], R, sigma)
+    achieved = flops / (p2p_ms / 1e3) / 1e12
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peak = 2 * 128 * sms * 2.070e9 / 1e12
@@ -329,7 +359,8 @@ def main():
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_p2p_f32",
-                     "pairs_per_launch": pairs, "flops_per_pair": FLOPS_PER_PAIR,
+                     "pairs_per_launch": pairs, "flops_per_launch": flops,
+                     "flops_per_pair": {"smoothed": FLOPS_PER_PAIR, "singular": FLOPS_PER_PAIR_SINGULAR},
                      "peak_basis": "2 x 128 FP32 lanes x %d SMs x 2070 MHz" % sms},
         "phases_ms": phases,
         "accuracy": out_err,

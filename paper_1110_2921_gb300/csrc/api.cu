@@ -371,6 +371,7 @@ int build_impl(Ctx *c, int64_t n, const void *x)
     if ((st = ensure(c, c->leaf_start, (size_t)(c->nleaf + 1) * sizeof(int), "leaf ranges"))) return st;
     if ((st = ensure(c, c->scan_part, (size_t)((c->nleaf + 1023) / 1024 + 1) * sizeof(int), "scan"))) return st;
     if ((st = ensure(c, c->maxleaf, sizeof(int), "max leaf"))) return st;
+    if ((st = ensure(c, c->bbox, (size_t)c->nleaf * 2 * sizeof(float4), "leaf boxes"))) return st;
     if (c->cfg.method == VFMM_METHOD_FMM) {
         c->lvl_off.assign(D + 2, 0);
         size_t tot = 0;
@@ -488,7 +489,7 @@ int vfmm_destroy(vfmm_handle h)
     Ctx *c = &h->c;
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->xs, &c->gs, &c->perm, &c->keys, &c->leaf_start, &c->counts, &c->fill, &c->tmpidx,
-                      &c->scan_part, &c->err, &c->maxleaf, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->ufar,
+                      &c->scan_part, &c->err, &c->maxleaf, &c->bbox, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->ufar,
                       &c->sfar, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->m2m_f64,
                       &c->lattice_f64, &c->root_m, &c->kblocks, &c->hx, &c->hg, &c->hu, &c->hs};
     for (DevBuf *b : bufs) release(*b);

@@ -82,8 +82,13 @@ int launch_gather_gamma(Ctx *c, const void *gamma)
 
 // ---------------------------------------------------------------------------------------
 // P2M (Eq. fmm3dm): Mh_n^m = s_nm sum_j gamma_j Y_n^m((x_j - z)/w) for each leaf.
-constexpr int P2M_TP = 32;
-constexpr int P2M_BS = 128;
+// One block per leaf: each thread evaluates the solid harmonics of one particle into shared
+// memory, then each thread owns two coefficients of all three components and sums over the
+// particles (a 3 x 64 by 64 x 128 product per chunk).
+template <typename T> struct P2MCfg {
+    static constexpr int TP = sizeof(T) == 4 ? 64 : 32;  // particles per chunk
+};
+constexpr int P2M_BS = 64;
 
 template <typename T>
 __global__ void __launch_bounds__(P2M_BS) k_p2m(const typename V4<T>::type *__restrict__ xs,
@@ -91,26 +96,28 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(const typename V4<T>::type *__re
                                                 const int *__restrict__ ls, int nside, int log2n, T w, int p, int pc,
                                                 T *__restrict__ M)
 {
+    constexpr int TP = P2MCfg<T>::TP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *Ysm = (T *)smem_raw;                 // [P2M_TP][pc]
-    T *gsm = Ysm + P2M_TP * pc;             // [P2M_TP][3]
+    T *Ysm = (T *)smem_raw;                 // [TP][pc]
+    typename V4<T>::type *gsm = (typename V4<T>::type *)(Ysm + TP * pc);  // [TP]
     const int leaf = blockIdx.x;
     const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
     const T zx = (cx + T(0.5)) * w, zy = (cy + T(0.5)) * w, zz = (cz + T(0.5)) * w;
     const T invw = T(1) / w;
     const int b = ls[leaf], e = ls[leaf + 1];
-    const int nout = 3 * pc;
-    T acc[4] = {0, 0, 0, 0};  // outputs tid + k * P2M_BS, 3*pc <= 4*P2M_BS for p <= 16 with pc <= 170
-    for (int s0 = b; s0 < e; s0 += P2M_TP) {
-        int cnt = min(P2M_TP, e - s0);
-        if (threadIdx.x < P2M_TP) {
-            T *row = Ysm + threadIdx.x * pc;
-            if (threadIdx.x < cnt) {
-                typename V4<T>::type xp = xs[s0 + threadIdx.x];
-                typename V4<T>::type gp = gs[s0 + threadIdx.x];
-                gsm[3 * threadIdx.x + 0] = gp.x;
-                gsm[3 * threadIdx.x + 1] = gp.y;
-                gsm[3 * threadIdx.x + 2] = gp.z;
+    const int nc = (p + 1) * (p + 1);
+    T acc[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[c][k] = 0;
+    for (int s0 = b; s0 < e; s0 += TP) {
+        const int cnt = min(TP, e - s0);
+        for (int t = threadIdx.x; t < TP; t += P2M_BS) {
+            T *row = Ysm + t * pc;
+            if (t < cnt) {
+                typename V4<T>::type xp = xs[s0 + t];
+                gsm[t] = gs[s0 + t];
                 T x = (xp.x - zx) * invw, y = (xp.y - zy) * invw, z = (xp.z - zz) * invw;
                 T r2 = x * x + y * y + z * z;
                 T dre = 1, dim = 0;
@@ -122,9 +129,9 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(const typename V4<T>::type *__re
                         dre = nre;
                         dim = nim;
                     }
-                    T s = sfac_t<T>(m, m);
-                    row[pk(m, m)] = dre * s;
-                    if (m > 0) row[pk(m, m) + 1] = dim * s;
+                    T sm = sfac_t<T>(m, m);
+                    row[pk(m, m)] = dre * sm;
+                    if (m > 0) row[pk(m, m) + 1] = dim * sm;
                     T pre = dre, pim = dim, ppre = 0, ppim = 0;
                     for (int n = m + 1; n <= p; ++n) {
                         T c1 = T(2 * n - 1) * z, f = rec_t<T>(n, m);
@@ -139,30 +146,31 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(const typename V4<T>::type *__re
                         pim = cim;
                     }
                 }
-                for (int j = (p + 1) * (p + 1); j < pc; ++j) row[j] = 0;
-            } else {
-                for (int j = 0; j < pc; ++j) row[j] = 0;
-                gsm[3 * threadIdx.x + 0] = 0;
-                gsm[3 * threadIdx.x + 1] = 0;
-                gsm[3 * threadIdx.x + 2] = 0;
+                for (int j = nc; j < pc; ++j) row[j] = 0;
             }
         }
         __syncthreads();
-        for (int k = 0; k < 4; ++k) {
-            int o = threadIdx.x + k * P2M_BS;
-            if (o < nout) {
-                int comp = o / pc, j = o - comp * pc;
-                T s = 0;
-                for (int t = 0; t < cnt; ++t) s += gsm[3 * t + comp] * Ysm[t * pc + j];
-                acc[k] += s;
+        for (int t = 0; t < cnt; ++t) {
+            typename V4<T>::type gv = gsm[t];
+            const T *row = Ysm + t * pc;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (threadIdx.x + k * P2M_BS < pc) {
+                    T yv = row[threadIdx.x + k * P2M_BS];
+                    acc[0][k] += gv.x * yv;
+                    acc[1][k] += gv.y * yv;
+                    acc[2][k] += gv.z * yv;
+                }
             }
         }
         __syncthreads();
     }
-    for (int k = 0; k < 4; ++k) {
-        int o = threadIdx.x + k * P2M_BS;
-        if (o < nout) M[(size_t)leaf * nout + o] = acc[k];
-    }
+    T *out = M + (size_t)leaf * 3 * pc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (threadIdx.x + k * P2M_BS < pc)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out[c * pc + threadIdx.x + k * P2M_BS] = acc[c][k];
 }
 
 int launch_p2m(Ctx *c)
@@ -170,7 +178,8 @@ int launch_p2m(Ctx *c)
     int log2n = 0;
     while ((1 << log2n) < c->nside) ++log2n;
     size_t off = c->lvl_off[c->depth];
-    size_t sm = (size_t)P2M_TP * c->pc * c->esz + P2M_TP * 3 * c->esz;
+    const int tp = c->f64 ? P2MCfg<double>::TP : P2MCfg<float>::TP;
+    size_t sm = (size_t)tp * c->pc * c->esz + (size_t)tp * 4 * c->esz;
     if (c->f64)
         k_p2m<double><<<(unsigned)c->nleaf, P2M_BS, sm, c->stream>>>(
             (const dvec4 *)c->xs.p, (const dvec4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,

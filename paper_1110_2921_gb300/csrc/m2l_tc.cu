@@ -29,12 +29,14 @@ constexpr int TC_THREADS = 128;
 constexpr int TC_CELLS = 64;
 constexpr int TC_N = 3 * TC_CELLS;          // 192 columns
 constexpr int TC_M = 128;
-constexpr int TC_STAGES = 4;
+constexpr int TC_STAGES = 5;
+constexpr int TC_PREFETCH = 3;               // stage i+3 refills the slot of MMA i-2
 constexpr int TC_KBYTES = 64;               // K bytes per stage per row
 constexpr int TC_A_BYTES = TC_M * TC_KBYTES;     // 8 KB
 constexpr int TC_B_BYTES = TC_N * TC_KBYTES;     // 12 KB
 constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 40 KB
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 2048;       // + alignment, barriers, tmem slot
+constexpr int TC_MAXKB = 256;                                    // k-blocks per parity (<= 189 used)
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 64 + TC_MAXKB * 16 + TC_CELLS * 4;
 constexpr int TC_TMEM_COLS = 256;
 constexpr long long TC_WAIT_LIMIT = 1LL << 26;
 
@@ -111,13 +113,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcParams tp)
     unsigned char *stages = base;
     uint64_t *bars = (uint64_t *)(base + TC_STAGES * TC_STAGE_BYTES);
     uint32_t *tmem_slot = (uint32_t *)(bars + TC_STAGES);
+    int4 *kb_s = (int4 *)(base + TC_STAGES * TC_STAGE_BYTES + 64);
+    int *cell_s = (int *)(kb_s + TC_MAXKB);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int g = blockIdx.y;
     const int n = tp.n, half = n >> 1;
     const int64_t cell0 = (int64_t)blockIdx.x * TC_CELLS;
-    const int nkb = tp.kb_cnt[g];
-    const int4 *kbl = tp.kb + tp.kb_off[g];
+    const int nkb = min(tp.kb_cnt[g], TC_MAXKB);
+    const int4 *kbl = kb_s;
+    for (int q = tid; q < nkb; q += TC_THREADS) kb_s[q] = tp.kb[tp.kb_off[g] + q];
+    for (int q = tid; q < TC_CELLS; q += TC_THREADS) {
+        int64_t P = cell0 + q;
+        int px = (int)(P / ((int64_t)half * half)), py = (int)((P / half) % half), pz = (int)(P % half);
+        int cx = 2 * px + ((g >> 2) & 1), cy = 2 * py + ((g >> 1) & 1), cz = 2 * pz + (g & 1);
+        cell_s[q] = (cx * n + cy) * n + cz;
+    }
     const int nchunk = tp.nchunk;
     const int nk = nkb * nchunk;
     const int pc = tp.pc;
@@ -191,31 +202,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcParams tp)
 
     // prologue
 #pragma unroll
-    for (int i = 0; i < TC_STAGES - 1; ++i) {
+    for (int i = 0; i < TC_PREFETCH; ++i) {
         if (i < nk) load_stage(i);
         cp_async_commit();
     }
     for (int i = 0; i < nk; ++i) {
         const int s = i % TC_STAGES;
-        const int ip = i + TC_STAGES - 1;
-        if (ip < nk) {
-            if (i >= 1) {
-                int pi = i - 1;
-                ok = mbar_wait(smem_u32(&bars[pi % TC_STAGES]), (uint32_t)((pi / TC_STAGES) & 1));
-            }
+        const int ip = i + TC_PREFETCH;
+        // the slot of stage ip was last read by the MMAs of iteration ip - TC_STAGES = i - 2
+        if (ip < nk && ip >= TC_STAGES) {
+            int pi = ip - TC_STAGES;
+            ok = mbar_wait(smem_u32(&bars[pi % TC_STAGES]), (uint32_t)((pi / TC_STAGES) & 1));
         }
-        // a bounded wait that gave up anywhere ends the loop in every thread
+        if (ip < nk && ok) load_stage(ip);
+        cp_async_commit();
+        cp_async_wait<TC_PREFETCH>();
+        fence_proxy_async();
+        // one barrier: stage i is complete in every thread, and every bounded wait succeeded
         if (!__syncthreads_and(ok ? 1 : 0)) {
             ok = false;
             break;
         }
-        if (ip < nk) {
-            load_stage(ip);
-        }
-        cp_async_commit();
-        cp_async_wait<TC_STAGES - 1>();
-        fence_proxy_async();
-        __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             unsigned char *st = stages + s * TC_STAGE_BYTES;
@@ -259,11 +266,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcParams tp)
             for (int e = 0; e < 16; ++e) {
                 int col = c0 + e;
                 int q = col / 3, comp = col - 3 * q;
-                int64_t P = cell0 + q;
-                int px = (int)(P / ((int64_t)half * half)), py = (int)((P / half) % half), pz = (int)(P % half);
-                int cx = 2 * px + ((g >> 2) & 1), cy = 2 * py + ((g >> 1) & 1), cz = 2 * pz + (g & 1);
-                int64_t cell = ((int64_t)cx * n + cy) * n + cz;
-                if (k < pc) C[(cell * 3 + comp) * pc + k] = __uint_as_float(r[e]);
+                C[((int64_t)cell_s[q] * 3 + comp) * pc + k] = __uint_as_float(r[e]);
             }
         }
     } else {

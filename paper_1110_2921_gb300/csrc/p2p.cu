@@ -52,6 +52,8 @@ struct P2PConst {
     float cf;      // sqrt(2/pi) / sigma^3
     float zs;      // series threshold on r2 * ce (rho < 0.5)
     float inv_s2;  // 1/sigma^2
+    float d2_series;    // leaf-pair squared gap below which the series branch may be needed
+    float d2_singular;  // leaf-pair squared gap above which the singular kernel is exact
     float ks;      // sqrt(2/pi) / sigma^3 (series K prefactor)
     float fs;      // sqrt(2/pi) / sigma^5 (series F prefactor)
 };
@@ -105,6 +107,85 @@ __device__ __forceinline__ void pair_f32(const P2PConst &k, float xi0, float xi1
     acc.b0 = fmaf(fg, w0, acc.b0);
     acc.b1 = fmaf(fg, w1, acc.b1);
     acc.b2 = fmaf(fg, w2, acc.b2);
+}
+
+// The same interaction without the small-rho series (valid when every pair of the two leaves
+// has rho >= 0.5, so r > 0 and the closed form has no cancellation trouble).
+__device__ __forceinline__ void pair_f32_smooth(const P2PConst &k, float xi0, float xi1, float xi2, float gi0,
+                                                float gi1, float gi2, float4 xj, float4 gj, Acc &acc)
+{
+    float dx = xi0 - xj.x, dy = xi1 - xj.y, dz = xi2 - xj.z;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float e = ex2_approx(r2 * k.ce);
+    float rinv = rsqrt_approx(r2);
+    float r = r2 * rinv;
+    float t = rcp_approx(fmaf(r, k.ct, 1.0f));
+    float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                          0.254829592f);
+    float q = fmaf(-e, fmaf(k.cq, r, poly), 1.0f);
+    float rinv2 = rinv * rinv;
+    float K = q * (rinv2 * rinv);
+    float F = rinv2 * fmaf(-3.0f, K, k.cf * e);
+    float w0 = gj.y * dz - gj.z * dy;
+    float w1 = gj.z * dx - gj.x * dz;
+    float w2 = gj.x * dy - gj.y * dx;
+    acc.u0 = fmaf(K, w0, acc.u0);
+    acc.u1 = fmaf(K, w1, acc.u1);
+    acc.u2 = fmaf(K, w2, acc.u2);
+    acc.a0 = fmaf(K, gj.x, acc.a0);
+    acc.a1 = fmaf(K, gj.y, acc.a1);
+    acc.a2 = fmaf(K, gj.z, acc.a2);
+    float fg = F * fmaf(gi0, dx, fmaf(gi1, dy, gi2 * dz));
+    acc.b0 = fmaf(fg, w0, acc.b0);
+    acc.b1 = fmaf(fg, w1, acc.b1);
+    acc.b2 = fmaf(fg, w2, acc.b2);
+}
+
+// Leaves whose closest pair has rho >= 6.5: q = 1 - O(1e-9) and the Gaussian term of F is
+// O(1e-7) relative, so the kernel is the singular Biot-Savart kernel to FP32 rounding
+// (K = 1/r^3, F = -3/r^5, before the common 1/(4 pi)).
+__device__ __forceinline__ void pair_f32_singular(float xi0, float xi1, float xi2, float gi0, float gi1, float gi2,
+                                                  float4 xj, float4 gj, Acc &acc)
+{
+    float dx = xi0 - xj.x, dy = xi1 - xj.y, dz = xi2 - xj.z;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float rinv = rsqrt_approx(r2);
+    float rinv2 = rinv * rinv;
+    float K = rinv2 * rinv;
+    float F = -3.0f * K * rinv2;
+    float w0 = gj.y * dz - gj.z * dy;
+    float w1 = gj.z * dx - gj.x * dz;
+    float w2 = gj.x * dy - gj.y * dx;
+    acc.u0 = fmaf(K, w0, acc.u0);
+    acc.u1 = fmaf(K, w1, acc.u1);
+    acc.u2 = fmaf(K, w2, acc.u2);
+    acc.a0 = fmaf(K, gj.x, acc.a0);
+    acc.a1 = fmaf(K, gj.y, acc.a1);
+    acc.a2 = fmaf(K, gj.z, acc.a2);
+    float fg = F * fmaf(gi0, dx, fmaf(gi1, dy, gi2 * dz));
+    acc.b0 = fmaf(fg, w0, acc.b0);
+    acc.b1 = fmaf(fg, w1, acc.b1);
+    acc.b2 = fmaf(fg, w2, acc.b2);
+}
+
+template <int MODE>
+__device__ __forceinline__ void source_tile(const P2PConst &kc, float xi0, float xi1, float xi2, float4 gi,
+                                            const float4 *sx, const float4 *sg, int cnt, Acc &acc)
+{
+    int j = 0;
+    for (; j + 4 <= cnt; j += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (MODE == 0) pair_f32(kc, xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j + u], sg[j + u], acc);
+            else if (MODE == 1) pair_f32_smooth(kc, xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j + u], sg[j + u], acc);
+            else pair_f32_singular(xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j + u], sg[j + u], acc);
+        }
+    }
+    for (; j < cnt; ++j) {
+        if (MODE == 0) pair_f32(kc, xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j], sg[j], acc);
+        else if (MODE == 1) pair_f32_smooth(kc, xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j], sg[j], acc);
+        else pair_f32_singular(xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j], sg[j], acc);
+    }
 }
 
 struct AccD {
@@ -176,10 +257,11 @@ constexpr float INV_4PI_F = 0.0795774715459476679f;
 constexpr double INV_4PI_D = 0.0795774715459476679;
 
 __global__ void __launch_bounds__(P2P_BS) k_p2p_f32(const float4 *__restrict__ xs, const float4 *__restrict__ gs,
-                                                    const int *__restrict__ ls, int nside, int log2n, int R,
-                                                    P2PConst kc, const float *__restrict__ ufar,
-                                                    const float *__restrict__ sfar, const int *__restrict__ perm,
-                                                    float *__restrict__ u_out, float *__restrict__ s_out)
+                                                    const int *__restrict__ ls, const float4 *__restrict__ bbox,
+                                                    int nside, int log2n, int R, P2PConst kc,
+                                                    const float *__restrict__ ufar, const float *__restrict__ sfar,
+                                                    const int *__restrict__ perm, float *__restrict__ u_out,
+                                                    float *__restrict__ s_out)
 {
     __shared__ float4 sx[P2P_BS];
     __shared__ float4 sg[P2P_BS];
@@ -187,6 +269,7 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p_f32(const float4 *__restrict__ x
     const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
     const int tb = ls[leaf], te = ls[leaf + 1];
     const float Lf = (float)kc.L;
+    const float4 tlo = bbox[2 * leaf], thi = bbox[2 * leaf + 1];
     for (int t0 = tb + blockIdx.y * P2P_BS; t0 < te; t0 += gridDim.y * P2P_BS) {
         const int ti = t0 + threadIdx.x;
         const bool active = ti < te;
@@ -198,10 +281,16 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p_f32(const float4 *__restrict__ x
                 for (int oz = -R; oz <= R; ++oz) {
                     int nx = cx + ox, ny = cy + oy, nz = cz + oz;
                     int sl = ((nx & (nside - 1)) * nside + (ny & (nside - 1))) * nside + (nz & (nside - 1));
-                    // target shifted by minus the source image offset
-                    float xi0 = xi.x - Lf * (float)(nx >> log2n);
-                    float xi1 = xi.y - Lf * (float)(ny >> log2n);
-                    float xi2 = xi.z - Lf * (float)(nz >> log2n);
+                    // image shift of this neighbour; the target is moved by minus the shift
+                    float shx = Lf * (float)(nx >> log2n), shy = Lf * (float)(ny >> log2n), shz = Lf * (float)(nz >> log2n);
+                    float xi0 = xi.x - shx, xi1 = xi.y - shy, xi2 = xi.z - shz;
+                    // closest approach of the two leaf boxes selects the inner loop (block-uniform)
+                    float4 slo = bbox[2 * sl], shi = bbox[2 * sl + 1];
+                    float gx = fmaxf(0.f, fmaxf(slo.x + shx - thi.x, tlo.x - shi.x - shx));
+                    float gy = fmaxf(0.f, fmaxf(slo.y + shy - thi.y, tlo.y - shi.y - shy));
+                    float gz = fmaxf(0.f, fmaxf(slo.z + shz - thi.z, tlo.z - shi.z - shz));
+                    float d2 = gx * gx + gy * gy + gz * gz;
+                    const int mode = d2 >= kc.d2_singular ? 2 : (d2 >= kc.d2_series ? 1 : 0);
                     int sb = ls[sl], se = ls[sl + 1];
                     for (int s0 = sb; s0 < se; s0 += P2P_BS) {
                         int cnt = min(P2P_BS, se - s0);
@@ -211,12 +300,9 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p_f32(const float4 *__restrict__ x
                             sg[threadIdx.x] = gs[s0 + threadIdx.x];
                         }
                         __syncthreads();
-                        int j = 0;
-                        for (; j + 4 <= cnt; j += 4) {
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) pair_f32(kc, xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j + u], sg[j + u], acc);
-                        }
-                        for (; j < cnt; ++j) pair_f32(kc, xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j], sg[j], acc);
+                        if (mode == 2) source_tile<2>(kc, xi0, xi1, xi2, gi, sx, sg, cnt, acc);
+                        else if (mode == 1) source_tile<1>(kc, xi0, xi1, xi2, gi, sx, sg, cnt, acc);
+                        else source_tile<0>(kc, xi0, xi1, xi2, gi, sx, sg, cnt, acc);
                     }
                 }
         if (active) {
@@ -326,8 +412,11 @@ int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, 
         kc.inv_s2 = (float)(1.0 / (sigma * sigma));
         kc.ks = (float)(cpi / (sigma * sigma * sigma));
         kc.fs = (float)(cpi / (sigma * sigma * sigma * sigma * sigma));
+        kc.d2_series = (float)(0.36 * sigma * sigma);      // (0.6 sigma)^2: margin over rho = 0.5
+        kc.d2_singular = (float)(42.25 * sigma * sigma);   // (6.5 sigma)^2
         k_p2p_f32<<<grid, P2P_BS, 0, c->stream>>>((const float4 *)c->xs.p, (const float4 *)c->gs.p,
-                                                  (const int *)c->leaf_start.p, c->nside, log2n, R, kc,
+                                                  (const int *)c->leaf_start.p, (const float4 *)c->bbox.p,
+                                                  c->nside, log2n, R, kc,
                                                   (const float *)ufar, (const float *)sfar, (const int *)c->perm.p,
                                                   (float *)u_out, (float *)s_out);
     }

@@ -123,13 +123,20 @@ __global__ void k_scatter(int64_t n, const int *__restrict__ keys, const int *__
 template <typename TIn, typename T>
 __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict__ tmpidx, const TIn *__restrict__ x,
                             double L, int *__restrict__ perm, typename V4<T>::type *__restrict__ xs,
-                            int *__restrict__ err)
+                            float4 *__restrict__ bbox, int *__restrict__ err)
 {
     __shared__ int s[LEAF_SORT_CAP];
+    __shared__ float red[6][8];
     int leaf = blockIdx.x;
     int b = start[leaf], e = start[leaf + 1];
     int cnt = e - b;
-    if (cnt <= 0) return;
+    if (cnt <= 0) {
+        if (threadIdx.x == 0) {
+            bbox[2 * leaf] = make_float4(3e38f, 3e38f, 3e38f, 0.f);
+            bbox[2 * leaf + 1] = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
+        }
+        return;
+    }
     if (cnt > LEAF_SORT_CAP) {
         if (threadIdx.x == 0) atomicOr(err, ERRBIT_LEAF_OVERFLOW);
         return;
@@ -154,6 +161,7 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
             __syncthreads();
         }
     double invL = 1.0 / L;
+    float mn[3] = {3e38f, 3e38f, 3e38f}, mx[3] = {-3e38f, -3e38f, -3e38f};
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
         int i = s[k];
         perm[b + k] = i;
@@ -161,6 +169,37 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
         T c1 = (T)wrap_coord<double>((double)x[3 * (int64_t)i + 1], L, invL);
         T c2 = (T)wrap_coord<double>((double)x[3 * (int64_t)i + 2], L, invL);
         xs[b + k] = make_v4<T>(c0, c1, c2, T(0));
+        float cf[3] = {(float)c0, (float)c1, (float)c2};
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fminf(mn[d], cf[d]);
+            mx[d] = fmaxf(mx[d], cf[d]);
+        }
+    }
+    // leaf bounding box (of the FP32-rounded positions the P2P kernel sees)
+    for (int d = 0; d < 3; ++d)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+        }
+    int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int d = 0; d < 3; ++d) {
+            red[d][w] = mn[d];
+            red[3 + d][w] = mx[d];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = red[d][0];
+            hi[d] = red[3 + d][0];
+            for (int q = 1; q < nw; ++q) {
+                lo[d] = fminf(lo[d], red[d][q]);
+                hi[d] = fmaxf(hi[d], red[3 + d][q]);
+            }
+        }
+        bbox[2 * leaf] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        bbox[2 * leaf + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
     }
 }
 
@@ -182,7 +221,8 @@ template <typename TIn, typename T> static int tree_impl(Ctx *c, const TIn *x)
     k_scatter<<<nb, 256, 0, st>>>(n, (int *)c->keys.p, start, (int *)c->fill.p, (int *)c->tmpidx.p);
     k_leaf_sort<TIn, T><<<(unsigned)nleaf, 256, 0, st>>>(start, (int *)c->tmpidx.p, x, c->cfg.box,
                                                          (int *)c->perm.p,
-                                                         (typename V4<T>::type *)c->xs.p, (int *)c->err.p);
+                                                         (typename V4<T>::type *)c->xs.p, (float4 *)c->bbox.p,
+                                                         (int *)c->err.p);
     c->launches += 5;  // k_keys, three scan kernels and k_scatter precede k_leaf_sort
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;

@@ -83,6 +83,7 @@ struct Ctx {
 
     // device buffers
     DevBuf xs, gs, perm, keys, leaf_start, counts, fill, tmpidx, scan_part, err, maxleaf;
+    DevBuf bbox;                   // per leaf: float4 lo, float4 hi of its particles
     DevBuf mexp, lexp;             // all levels, T
     DevBuf mhi, mlo;               // tensor-core copies of the multipoles (largest level)
     DevBuf ufar, sfar;             // far-field u, S in sorted order, T
