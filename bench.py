@@ -28,8 +28,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particles/s for u+stretching at 256³ (p=10), rel-L2 err vs FP64 direct sum"
 PAPER_PARTICLES_PER_S = 0.84e6   # 256^3 / 20 s per step at p=10 on one C2070 (paper, Section 4.1)
-FLOPS_PER_PAIR = 65              # FP32 operations of one smoothed P2P pair (FMA = 2), + 3 MUFU
-FLOPS_PER_PAIR_SINGULAR = 45     # a pair of leaves >= 6.5 sigma apart (singular kernel), + 1 MUFU
+FLOPS_PER_PAIR = 61              # FP32 operations of one smoothed P2P pair (FMA = 2), + 3 MUFU
+FLOPS_PER_PAIR_SINGULAR = 42     # a pair of leaves >= 6.5 sigma apart (singular kernel), + 1 MUFU
 
 
 def parse():
@@ -106,7 +106,7 @@ class ClockSampler:
 
 def p2p_work(x, L, depth, R, sigma):
     """Pairs the P2P visits, split as the kernel splits them by leaf-box separation d:
-    d < 6.5 sigma -> smoothed kernel (65 flops), d >= 6.5 sigma -> singular kernel (45 flops).
+    d < 6.5 sigma -> smoothed kernel (61 flops), d >= 6.5 sigma -> singular kernel (42 flops).
     Returns (pairs, flops)."""
     import itertools
     import numpy as np

@@ -331,7 +331,7 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out)
         for (int k = 3; k <= 7; ++k) cudaEventRecord(c->ev[k], st);
     }
     cudaEventRecord(c->ev[8], st);
-    if ((rc = launch_p2p(c, R, sigma, uf, sf, u_out, s_out, 0))) return rc;
+    if ((rc = launch_p2p(c, R, sigma, uf, sf, u_out, s_out, fmm ? -1 : c->cfg.direct_images))) return rc;
     cudaEventRecord(c->ev[9], st);
     c->timed_eval = true;
     return VFMM_OK;
@@ -343,9 +343,7 @@ int build_impl(Ctx *c, int64_t n, const void *x)
     if (n > (int64_t)1 << 30) return fail(c, VFMM_ERR_UNSUPPORTED, "n above 2^30 particles");
     if (!x) return fail(c, VFMM_ERR_ARG, "null x");
     int D;
-    if (c->cfg.method == VFMM_METHOD_DIRECT) {
-        D = 0;
-    } else if (c->cfg.depth > 0) {
+    if (c->cfg.depth > 0) {
         D = c->cfg.depth;
     } else {
         double ratio = (double)n / (double)(c->cfg.ncrit > 0 ? c->cfg.ncrit : 64);
@@ -438,6 +436,7 @@ int vfmm_create(const vfmm_config *cfg, vfmm_handle *out)
     if (k.dtype != VFMM_F32 && k.dtype != VFMM_F64) return VFMM_ERR_ARG;
     if (k.method != VFMM_METHOD_FMM && k.method != VFMM_METHOD_DIRECT) return VFMM_ERR_ARG;
     if (!(k.box > 0.0) || !std::isfinite(k.box)) return VFMM_ERR_ARG;
+    if (k.depth < 0 || k.depth > MAX_DEPTH) return VFMM_ERR_ARG;
     if (k.method == VFMM_METHOD_FMM) {
         if (k.p < 2) return VFMM_ERR_ARG;
         if ((k.p + 1) * (k.p + 1) > OUT_ROWS) return VFMM_ERR_UNSUPPORTED;

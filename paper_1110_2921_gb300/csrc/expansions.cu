@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(const typename V4<T>::type *__re
             }
         }
         __syncthreads();
+#pragma unroll 8
         for (int t = 0; t < cnt; ++t) {
             typename V4<T>::type gv = gsm[t];
             const T *row = Ysm + t * pc;

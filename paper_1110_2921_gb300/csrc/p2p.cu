@@ -22,6 +22,8 @@
 #include "common.cuh"
 #include "vfmm_internal.h"
 
+#include <cmath>
+
 namespace vfmm {
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -109,82 +111,92 @@ __device__ __forceinline__ void pair_f32(const P2PConst &k, float xi0, float xi1
     acc.b2 = fmaf(fg, w2, acc.b2);
 }
 
-// The same interaction without the small-rho series (valid when every pair of the two leaves
-// has rho >= 0.5, so r > 0 and the closed form has no cancellation trouble).
-__device__ __forceinline__ void pair_f32_smooth(const P2PConst &k, float xi0, float xi1, float xi2, float gi0,
-                                                float gi1, float gi2, float4 xj, float4 gj, Acc &acc)
-{
-    float dx = xi0 - xj.x, dy = xi1 - xj.y, dz = xi2 - xj.z;
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float e = ex2_approx(r2 * k.ce);
-    float rinv = rsqrt_approx(r2);
-    float r = r2 * rinv;
-    float t = rcp_approx(fmaf(r, k.ct, 1.0f));
-    float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
-                          0.254829592f);
-    float q = fmaf(-e, fmaf(k.cq, r, poly), 1.0f);
-    float rinv2 = rinv * rinv;
-    float K = q * (rinv2 * rinv);
-    float F = rinv2 * fmaf(-3.0f, K, k.cf * e);
-    float w0 = gj.y * dz - gj.z * dy;
-    float w1 = gj.z * dx - gj.x * dz;
-    float w2 = gj.x * dy - gj.y * dx;
-    acc.u0 = fmaf(K, w0, acc.u0);
-    acc.u1 = fmaf(K, w1, acc.u1);
-    acc.u2 = fmaf(K, w2, acc.u2);
-    acc.a0 = fmaf(K, gj.x, acc.a0);
-    acc.a1 = fmaf(K, gj.y, acc.a1);
-    acc.a2 = fmaf(K, gj.z, acc.a2);
-    float fg = F * fmaf(gi0, dx, fmaf(gi1, dy, gi2 * dz));
-    acc.b0 = fmaf(fg, w0, acc.b0);
-    acc.b1 = fmaf(fg, w1, acc.b1);
-    acc.b2 = fmaf(fg, w2, acc.b2);
-}
+// --- FP32 near-field kernel in scaled, leaf-relative coordinates -------------------------
+// Positions enter as x^ = s (x - z_t), z_t the target leaf centre, s = sqrt(log2(e)/(2 sigma^2)),
+// so that exp(-rho^2/2) = 2^(-|r^|^2) needs no multiply; every other sigma factor folds into
+// constants.  With c_j = gamma_j x x^_j (formed once per source when it is staged),
+//   sum K gamma_j x r^ = A x x^_i - U,         A = sum K gamma_j,   U = sum K c_j,
+//   sum f (gamma_j x r^) = D x x^_i - E,       D = sum f gamma_j,   E = sum f c_j,
+// with f = F (gamma_i . r^), which saves the per-pair cross product.  Leaf-relative
+// coordinates keep |x^_i| within a few |r^| of the nearest pairs, so the rearrangement costs
+// at most a few FP32 ulps.
+struct P3Const {
+    float s;           // coordinate scale
+    float ct;          // A&S p / (sqrt2 sigma s)
+    float cq;          // sqrt(2/pi) / (sigma s)
+    float cf;          // sqrt(2/pi) / (sigma^3 s^3)
+    float r2s;         // |r^|^2 below which rho < 0.5
+    float inv_s2;      // 1 / (sigma s)^2: rho^2 = |r^|^2 inv_s2
+    float ks, fs;      // series prefactors sqrt(2/pi)/(sigma s)^3 and /(sigma s)^5
+    float d2_series;   // leaf-box squared gap (true units) below which rho < 0.5 may occur
+    float d2_singular; // leaf-box squared gap (true units) above which rho >= 6.5
+    float L;
+};
 
-// Leaves whose closest pair has rho >= 6.5: q = 1 - O(1e-9) and the Gaussian term of F is
-// O(1e-7) relative, so the kernel is the singular Biot-Savart kernel to FP32 rounding
-// (K = 1/r^3, F = -3/r^5, before the common 1/(4 pi)).
-__device__ __forceinline__ void pair_f32_singular(float xi0, float xi1, float xi2, float gi0, float gi1, float gi2,
-                                                  float4 xj, float4 gj, Acc &acc)
-{
-    float dx = xi0 - xj.x, dy = xi1 - xj.y, dz = xi2 - xj.z;
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float rinv = rsqrt_approx(r2);
-    float rinv2 = rinv * rinv;
-    float K = rinv2 * rinv;
-    float F = -3.0f * K * rinv2;
-    float w0 = gj.y * dz - gj.z * dy;
-    float w1 = gj.z * dx - gj.x * dz;
-    float w2 = gj.x * dy - gj.y * dx;
-    acc.u0 = fmaf(K, w0, acc.u0);
-    acc.u1 = fmaf(K, w1, acc.u1);
-    acc.u2 = fmaf(K, w2, acc.u2);
-    acc.a0 = fmaf(K, gj.x, acc.a0);
-    acc.a1 = fmaf(K, gj.y, acc.a1);
-    acc.a2 = fmaf(K, gj.z, acc.a2);
-    float fg = F * fmaf(gi0, dx, fmaf(gi1, dy, gi2 * dz));
-    acc.b0 = fmaf(fg, w0, acc.b0);
-    acc.b1 = fmaf(fg, w1, acc.b1);
-    acc.b2 = fmaf(fg, w2, acc.b2);
-}
+struct Acc3 {
+    float A0, A1, A2, U0, U1, U2, D0, D1, D2, E0, E1, E2;
+};
 
 template <int MODE>
-__device__ __forceinline__ void source_tile(const P2PConst &kc, float xi0, float xi1, float xi2, float4 gi,
-                                            const float4 *sx, const float4 *sg, int cnt, Acc &acc)
+__device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, float xi2, float gi0, float gi1, float gi2,
+                                      const float4 &xj, const float4 &gj, const float4 &cj, Acc3 &a)
 {
-    int j = 0;
-    for (; j + 4 <= cnt; j += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (MODE == 0) pair_f32(kc, xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j + u], sg[j + u], acc);
-            else if (MODE == 1) pair_f32_smooth(kc, xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j + u], sg[j + u], acc);
-            else pair_f32_singular(xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j + u], sg[j + u], acc);
+    float dx = xi0 - xj.x, dy = xi1 - xj.y, dz = xi2 - xj.z;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float K, F;
+    if (MODE == 2) {  // singular kernel: K = 1/r^3, F = -3/r^5
+        float rinv = rsqrt_approx(r2);
+        float rinv2 = rinv * rinv;
+        K = rinv2 * rinv;
+        F = -3.0f * K * rinv2;
+    } else {
+        float e = ex2_approx(-r2);
+        float rinv = rsqrt_approx(r2);
+        float r = r2 * rinv;
+        float t = rcp_approx(fmaf(r, k.ct, 1.0f));
+        float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                              0.254829592f);
+        float q = fmaf(-e, fmaf(k.cq, r, poly), 1.0f);
+        float rinv2 = rinv * rinv;
+        K = q * (rinv2 * rinv);
+        F = rinv2 * fmaf(-3.0f, K, k.cf * e);
+        if (MODE == 0) {
+            if (r2 < k.r2s) {  // rho < 0.5, including the self pair
+                float x = r2 * k.inv_s2;
+                K = k.ks * series_k<float>(x);
+                F = k.fs * series_f<float>(x);
+            }
         }
     }
-    for (; j < cnt; ++j) {
-        if (MODE == 0) pair_f32(kc, xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j], sg[j], acc);
-        else if (MODE == 1) pair_f32_smooth(kc, xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j], sg[j], acc);
-        else pair_f32_singular(xi0, xi1, xi2, gi.x, gi.y, gi.z, sx[j], sg[j], acc);
+    a.A0 = fmaf(K, gj.x, a.A0);
+    a.A1 = fmaf(K, gj.y, a.A1);
+    a.A2 = fmaf(K, gj.z, a.A2);
+    a.U0 = fmaf(K, cj.x, a.U0);
+    a.U1 = fmaf(K, cj.y, a.U1);
+    a.U2 = fmaf(K, cj.z, a.U2);
+    float f = F * fmaf(gi0, dx, fmaf(gi1, dy, gi2 * dz));
+    a.D0 = fmaf(f, gj.x, a.D0);
+    a.D1 = fmaf(f, gj.y, a.D1);
+    a.D2 = fmaf(f, gj.z, a.D2);
+    a.E0 = fmaf(f, cj.x, a.E0);
+    a.E1 = fmaf(f, cj.y, a.E1);
+    a.E2 = fmaf(f, cj.z, a.E2);
+}
+
+constexpr int P3_THREADS = 32;   // one warp per target leaf chunk
+constexpr int P3_TPT = 2;        // targets per thread
+constexpr int P3_TILE = 64;      // staged sources
+
+template <int MODE>
+__device__ __forceinline__ void tile3(const P3Const &k, const float (&xi)[P3_TPT][3], const float (&gi)[P3_TPT][3],
+                                      const float4 *sx, const float4 *sg, const float4 *sc, int cnt,
+                                      Acc3 (&acc)[P3_TPT])
+{
+#pragma unroll 2
+    for (int j = 0; j < cnt; ++j) {
+        float4 xj = sx[j], gj = sg[j], cj = sc[j];
+#pragma unroll
+        for (int q = 0; q < P3_TPT; ++q) pair3<MODE>(k, xi[q][0], xi[q][1], xi[q][2], gi[q][0], gi[q][1], gi[q][2], xj, gj, cj, acc[q]);
     }
 }
 
@@ -256,34 +268,55 @@ constexpr int P2P_BS = 64;
 constexpr float INV_4PI_F = 0.0795774715459476679f;
 constexpr double INV_4PI_D = 0.0795774715459476679;
 
-__global__ void __launch_bounds__(P2P_BS) k_p2p_f32(const float4 *__restrict__ xs, const float4 *__restrict__ gs,
-                                                    const int *__restrict__ ls, const float4 *__restrict__ bbox,
-                                                    int nside, int log2n, int R, P2PConst kc,
-                                                    const float *__restrict__ ufar, const float *__restrict__ sfar,
-                                                    const int *__restrict__ perm, float *__restrict__ u_out,
-                                                    float *__restrict__ s_out)
+__global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict__ xs, const float4 *__restrict__ gs,
+                                                        const int *__restrict__ ls, const float4 *__restrict__ bbox,
+                                                        int nside, int log2n, int R, int direct_K, float leaf_w,
+                                                        P3Const kc,
+                                                        const float *__restrict__ ufar, const float *__restrict__ sfar,
+                                                        const int *__restrict__ perm, float *__restrict__ u_out,
+                                                        float *__restrict__ s_out)
 {
-    __shared__ float4 sx[P2P_BS];
-    __shared__ float4 sg[P2P_BS];
+    __shared__ float4 sx[P3_TILE], sg[P3_TILE], sc[P3_TILE];
     const int leaf = blockIdx.x;
     const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
     const int tb = ls[leaf], te = ls[leaf + 1];
-    const float Lf = (float)kc.L;
+    const float zx = (cx + 0.5f) * leaf_w, zy = (cy + 0.5f) * leaf_w, zz = (cz + 0.5f) * leaf_w;
+    const float s = kc.s;
     const float4 tlo = bbox[2 * leaf], thi = bbox[2 * leaf + 1];
-    for (int t0 = tb + blockIdx.y * P2P_BS; t0 < te; t0 += gridDim.y * P2P_BS) {
-        const int ti = t0 + threadIdx.x;
-        const bool active = ti < te;
-        float4 xi = active ? xs[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 gi = active ? gs[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
-        Acc acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int ox = -R; ox <= R; ++ox)
-            for (int oy = -R; oy <= R; ++oy)
-                for (int oz = -R; oz <= R; ++oz) {
+    const int per_block = P3_THREADS * P3_TPT;
+    for (int t0 = tb + blockIdx.y * per_block; t0 < te; t0 += gridDim.y * per_block) {
+        float xi[P3_TPT][3], gi[P3_TPT][3];
+        int tix[P3_TPT];
+#pragma unroll
+        for (int q = 0; q < P3_TPT; ++q) {
+            int ti = t0 + threadIdx.x + q * P3_THREADS;
+            tix[q] = ti;
+            float4 x = ti < te ? xs[ti] : make_float4(zx, zy, zz, 0.f);
+            float4 g = ti < te ? gs[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
+            xi[q][0] = s * (x.x - zx);
+            xi[q][1] = s * (x.y - zy);
+            xi[q][2] = s * (x.z - zz);
+            gi[q][0] = g.x;
+            gi[q][1] = g.y;
+            gi[q][2] = g.z;
+        }
+        Acc3 acc[P3_TPT];
+#pragma unroll
+        for (int q = 0; q < P3_TPT; ++q) acc[q] = Acc3{0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        // neighbour offsets: the (2R+1)^3 near field, or for the direct sum every leaf of the
+        // (2K+1)^3 image boxes
+        int lo[3], hi[3];
+        const int cc[3] = {cx, cy, cz};
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = direct_K >= 0 ? -cc[d] - direct_K * nside : -R;
+            hi[d] = direct_K >= 0 ? nside - 1 - cc[d] + direct_K * nside : R;
+        }
+        for (int ox = lo[0]; ox <= hi[0]; ++ox)
+            for (int oy = lo[1]; oy <= hi[1]; ++oy)
+                for (int oz = lo[2]; oz <= hi[2]; ++oz) {
                     int nx = cx + ox, ny = cy + oy, nz = cz + oz;
                     int sl = ((nx & (nside - 1)) * nside + (ny & (nside - 1))) * nside + (nz & (nside - 1));
-                    // image shift of this neighbour; the target is moved by minus the shift
-                    float shx = Lf * (float)(nx >> log2n), shy = Lf * (float)(ny >> log2n), shz = Lf * (float)(nz >> log2n);
-                    float xi0 = xi.x - shx, xi1 = xi.y - shy, xi2 = xi.z - shz;
+                    float shx = kc.L * (float)(nx >> log2n), shy = kc.L * (float)(ny >> log2n), shz = kc.L * (float)(nz >> log2n);
                     // closest approach of the two leaf boxes selects the inner loop (block-uniform)
                     float4 slo = bbox[2 * sl], shi = bbox[2 * sl + 1];
                     float gx = fmaxf(0.f, fmaxf(slo.x + shx - thi.x, tlo.x - shi.x - shx));
@@ -291,28 +324,39 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p_f32(const float4 *__restrict__ x
                     float gz = fmaxf(0.f, fmaxf(slo.z + shz - thi.z, tlo.z - shi.z - shz));
                     float d2 = gx * gx + gy * gy + gz * gz;
                     const int mode = d2 >= kc.d2_singular ? 2 : (d2 >= kc.d2_series ? 1 : 0);
+                    // sources relative to the target leaf centre, with the image shift
+                    float ox0 = shx - zx, ox1 = shy - zy, ox2 = shz - zz;
                     int sb = ls[sl], se = ls[sl + 1];
-                    for (int s0 = sb; s0 < se; s0 += P2P_BS) {
-                        int cnt = min(P2P_BS, se - s0);
-                        __syncthreads();
-                        if (threadIdx.x < cnt) {
-                            sx[threadIdx.x] = xs[s0 + threadIdx.x];
-                            sg[threadIdx.x] = gs[s0 + threadIdx.x];
+                    for (int s0 = sb; s0 < se; s0 += P3_TILE) {
+                        int cnt = min(P3_TILE, se - s0);
+                        __syncwarp();
+                        for (int j = threadIdx.x; j < cnt; j += P3_THREADS) {
+                            float4 x = xs[s0 + j], g = gs[s0 + j];
+                            float a0 = s * (x.x + ox0), a1 = s * (x.y + ox1), a2 = s * (x.z + ox2);
+                            sx[j] = make_float4(a0, a1, a2, 0.f);
+                            sg[j] = g;
+                            sc[j] = make_float4(g.y * a2 - g.z * a1, g.z * a0 - g.x * a2, g.x * a1 - g.y * a0, 0.f);
                         }
-                        __syncthreads();
-                        if (mode == 2) source_tile<2>(kc, xi0, xi1, xi2, gi, sx, sg, cnt, acc);
-                        else if (mode == 1) source_tile<1>(kc, xi0, xi1, xi2, gi, sx, sg, cnt, acc);
-                        else source_tile<0>(kc, xi0, xi1, xi2, gi, sx, sg, cnt, acc);
+                        __syncwarp();
+                        if (mode == 2) tile3<2>(kc, xi, gi, sx, sg, sc, cnt, acc);
+                        else if (mode == 1) tile3<1>(kc, xi, gi, sx, sg, sc, cnt, acc);
+                        else tile3<0>(kc, xi, gi, sx, sg, sc, cnt, acc);
                     }
                 }
-        if (active) {
-            float s0 = fmaf(acc.a1, gi.z, fmaf(-acc.a2, gi.y, acc.b0));
-            float s1 = fmaf(acc.a2, gi.x, fmaf(-acc.a0, gi.z, acc.b1));
-            float s2 = fmaf(acc.a0, gi.y, fmaf(-acc.a1, gi.x, acc.b2));
-            float u0 = acc.u0 * INV_4PI_F, u1 = acc.u1 * INV_4PI_F, u2 = acc.u2 * INV_4PI_F;
-            s0 *= INV_4PI_F;
-            s1 *= INV_4PI_F;
-            s2 *= INV_4PI_F;
+        // u = s^2 (A x x^ - U), S = s^3 (A x gamma + D x x^ - E), times 1/(4 pi)
+        const float su = INV_4PI_F * s * s, ss = su * s;
+#pragma unroll
+        for (int q = 0; q < P3_TPT; ++q) {
+            int ti = tix[q];
+            if (ti >= te) continue;
+            const Acc3 &a = acc[q];
+            const float *x = xi[q], *g = gi[q];
+            float u0 = su * (a.A1 * x[2] - a.A2 * x[1] - a.U0);
+            float u1 = su * (a.A2 * x[0] - a.A0 * x[2] - a.U1);
+            float u2 = su * (a.A0 * x[1] - a.A1 * x[0] - a.U2);
+            float s0 = ss * (a.A1 * g[2] - a.A2 * g[1] + a.D1 * x[2] - a.D2 * x[1] - a.E0);
+            float s1 = ss * (a.A2 * g[0] - a.A0 * g[2] + a.D2 * x[0] - a.D0 * x[2] - a.E1);
+            float s2 = ss * (a.A0 * g[1] - a.A1 * g[0] + a.D0 * x[1] - a.D1 * x[0] - a.E2);
             if (ufar) {
                 u0 += ufar[3 * (int64_t)ti + 0];
                 u1 += ufar[3 * (int64_t)ti + 1];
@@ -328,7 +372,8 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p_f32(const float4 *__restrict__ x
 
 __global__ void __launch_bounds__(P2P_BS) k_p2p_f64(const dvec4 *__restrict__ xs, const dvec4 *__restrict__ gs,
                                                     const int *__restrict__ ls, int nside, int log2n, int R,
-                                                    double sigma, double L, const double *__restrict__ ufar,
+                                                    int direct_K, double sigma, double L,
+                                                    const double *__restrict__ ufar,
                                                     const double *__restrict__ sfar, const int *__restrict__ perm,
                                                     double *__restrict__ u_out, double *__restrict__ s_out)
 {
@@ -344,9 +389,15 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p_f64(const dvec4 *__restrict__ xs
         dvec4 xi = active ? xs[ti] : z4;
         dvec4 gi = active ? gs[ti] : z4;
         AccD acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int ox = -R; ox <= R; ++ox)
-            for (int oy = -R; oy <= R; ++oy)
-                for (int oz = -R; oz <= R; ++oz) {
+        int lo[3], hi[3];
+        const int cc[3] = {cx, cy, cz};
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = direct_K >= 0 ? -cc[d] - direct_K * nside : -R;
+            hi[d] = direct_K >= 0 ? nside - 1 - cc[d] + direct_K * nside : R;
+        }
+        for (int ox = lo[0]; ox <= hi[0]; ++ox)
+            for (int oy = lo[1]; oy <= hi[1]; ++oy)
+                for (int oz = lo[2]; oz <= hi[2]; ++oz) {
                     int nx = cx + ox, ny = cy + oy, nz = cz + oz;
                     int sl = ((nx & (nside - 1)) * nside + (ny & (nside - 1))) * nside + (nz & (nside - 1));
                     double xi0 = xi.x - L * (double)(nx >> log2n);
@@ -385,7 +436,8 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p_f64(const dvec4 *__restrict__ xs
     }
 }
 
-int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, void *u_out, void *s_out, int)
+int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, void *u_out, void *s_out,
+               int direct_K)
 {
     int log2n = 0;
     while ((1 << log2n) < c->nside) ++log2n;
@@ -395,30 +447,36 @@ int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, 
     dim3 grid((unsigned)c->nleaf, (unsigned)chunks);
     if (c->f64) {
         k_p2p_f64<<<grid, P2P_BS, 0, c->stream>>>((const dvec4 *)c->xs.p, (const dvec4 *)c->gs.p,
-                                                  (const int *)c->leaf_start.p, c->nside, log2n, R, sigma,
-                                                  c->cfg.box, (const double *)ufar, (const double *)sfar,
+                                                  (const int *)c->leaf_start.p, c->nside, log2n, R, direct_K,
+                                                  sigma, c->cfg.box, (const double *)ufar, (const double *)sfar,
                                                   (const int *)c->perm.p, (double *)u_out, (double *)s_out);
     } else {
-        P2PConst kc;
-        kc.sigma = sigma;
-        kc.L = c->cfg.box;
         const double log2e = 1.4426950408889634074;
         const double cpi = 0.79788456080286535588;
-        kc.ce = (float)(-log2e / (2.0 * sigma * sigma));
-        kc.ct = (float)(0.3275911 / (1.41421356237309504880 * sigma));
-        kc.cq = (float)(cpi / sigma);
-        kc.cf = (float)(cpi / (sigma * sigma * sigma));
-        kc.zs = (float)(-0.25 * log2e / 2.0);
-        kc.inv_s2 = (float)(1.0 / (sigma * sigma));
-        kc.ks = (float)(cpi / (sigma * sigma * sigma));
-        kc.fs = (float)(cpi / (sigma * sigma * sigma * sigma * sigma));
+        const double sc = std::sqrt(log2e / (2.0 * sigma * sigma));
+        const double ss = sigma * sc;
+        P3Const kc;
+        kc.s = (float)sc;
+        kc.ct = (float)(0.3275911 / (1.41421356237309504880 * ss));
+        kc.cq = (float)(cpi / ss);
+        kc.cf = (float)(cpi / (ss * ss * ss));
+        kc.r2s = (float)(0.25 * ss * ss);
+        kc.inv_s2 = (float)(1.0 / (ss * ss));
+        kc.ks = (float)(cpi / (ss * ss * ss));
+        kc.fs = (float)(cpi / (ss * ss * ss * ss * ss));
         kc.d2_series = (float)(0.36 * sigma * sigma);      // (0.6 sigma)^2: margin over rho = 0.5
         kc.d2_singular = (float)(42.25 * sigma * sigma);   // (6.5 sigma)^2
-        k_p2p_f32<<<grid, P2P_BS, 0, c->stream>>>((const float4 *)c->xs.p, (const float4 *)c->gs.p,
-                                                  (const int *)c->leaf_start.p, (const float4 *)c->bbox.p,
-                                                  c->nside, log2n, R, kc,
-                                                  (const float *)ufar, (const float *)sfar, (const int *)c->perm.p,
-                                                  (float *)u_out, (float *)s_out);
+        kc.L = (float)c->cfg.box;
+        const int per_block = P3_THREADS * P3_TPT;
+        int chunks3 = (c->max_leaf + per_block - 1) / per_block;
+        if (chunks3 < 1) chunks3 = 1;
+        if (chunks3 > 65535) chunks3 = 65535;
+        dim3 grid3((unsigned)c->nleaf, (unsigned)chunks3);
+        k_p2p_f32<<<grid3, P3_THREADS, 0, c->stream>>>((const float4 *)c->xs.p, (const float4 *)c->gs.p,
+                                                       (const int *)c->leaf_start.p, (const float4 *)c->bbox.p,
+                                                       c->nside, log2n, R, direct_K, (float)c->leaf_w, kc,
+                                                       (const float *)ufar, (const float *)sfar, (const int *)c->perm.p,
+                                                       (float *)u_out, (float *)s_out);
     }
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;

@@ -114,8 +114,9 @@ int launch_p2m(Ctx *c);
 int launch_gemm(Ctx *c, const GemmParams &gp, int ngroups, int64_t ncell_group);
 int launch_root(Ctx *c);
 int launch_l2p(Ctx *c);
+// direct_K >= 0: direct sum over every leaf of the (2K+1)^3 image boxes; -1: the FMM near field (R rings)
 int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, void *u_out,
-               void *s_out, int images_only_direct);
+               void *s_out, int direct_K);
 int launch_tc_m2l(Ctx *c, int level, const int4 *kb_dev, const int *kb_off, const int *kb_cnt, bool bf16);
 int launch_split(Ctx *c, int level, bool bf16);
 void set_constants(int p);
