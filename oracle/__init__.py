@@ -10,6 +10,7 @@ Contents
   periodic image boxes, Eqs. (biotsavart), (cutoff), (stretching) and the image count of
   Section 4.1.  Optional full velocity gradient.
 * ``spectral``: the fully periodic field as a Fourier series (independent of the direct sum).
+* ``gradient``: dL/dgamma and dL/dx of L = sum |u - u*|^2 from the direct sums.
 
 Parity status: every function here is pinned by the ``tests/test_oracle_*.py`` checks
 (closed forms, quadrature, mpmath brute force, invariants, spectral cross-check).
@@ -96,3 +97,4 @@ def direct(x, gamma, sigma, L=2 * np.pi, K=1, targets=None, kmin=0, grad=False,
 
 
 from . import spectral  # noqa: E402,F401
+from . import gradient  # noqa: E402,F401

@@ -264,3 +264,28 @@ def test_coincident_distinct_particles_take_the_smooth_limit():
     d = 1e-7 * sigma * g[0] / np.linalg.norm(g[0])
     u2, S2 = oracle.direct(x[1:], g[1:], sigma, K=0, xt=(x[0] + d)[None], gt=g[:1])
     assert np.allclose(S2[0], S[0], rtol=1e-9)
+
+
+def test_loss_gradient_matches_central_differences():
+    # dL/dgamma = A w and dL/dx = (grad u^g)^T w + (grad u^w)^T g, against the oracle's own
+    # central differences of L = sum |u - u*|^2 (one image layer, 27 jittered particles)
+    n = 3
+    h = 2 * np.pi / n
+    x = wl.jitter(wl.lattice_positions(n), h, 0.3, seed=12)
+    rng = np.random.default_rng(13)
+    g = rng.normal(size=x.shape)
+    sigma = 0.9 * h
+    ustar = rng.normal(size=x.shape) * 0.1
+    dg, dx, _ = oracle.gradient.loss_gradient(x, g, sigma, ustar, K=1)
+    eps = 1e-6
+    for (i, a) in [(0, 0), (4, 2), (13, 1), (26, 0)]:
+        gp, gm = g.copy(), g.copy()
+        gp[i, a] += eps
+        gm[i, a] -= eps
+        fd = (oracle.gradient.loss(x, gp, sigma, ustar) - oracle.gradient.loss(x, gm, sigma, ustar)) / (2 * eps)
+        assert abs(fd - dg[i, a]) < 1e-7 * max(1.0, abs(fd)), (i, a, fd, dg[i, a])
+        xp, xm = x.copy(), x.copy()
+        xp[i, a] += eps
+        xm[i, a] -= eps
+        fd = (oracle.gradient.loss(xp, g, sigma, ustar) - oracle.gradient.loss(xm, g, sigma, ustar)) / (2 * eps)
+        assert abs(fd - dx[i, a]) < 1e-7 * max(1.0, abs(fd)), (i, a, fd, dx[i, a])
