@@ -115,6 +115,25 @@ int vfmm_build_tree(vfmm_handle h, int64_t n, const void *x);
 int vfmm_eval_velocity_stretching(vfmm_handle h, const void *gamma, double sigma, void *u_out,
                                   void *s_out);
 
+/* Velocity and its gradient at every particle: u_out n x 3 and g_out n x 9 with
+ * g_out[9 i + 3 a + k] = du_a/dx_k at x_i (device, caller order).  Same sum as
+ * vfmm_eval_velocity_stretching (S_i = G_i gamma_i); the self pair is excluded.  Used by the
+ * adjoint and by callers that need the full tensor (e.g. the transpose stretching scheme).
+ * Errors as vfmm_eval_velocity_stretching. */
+int vfmm_eval_velocity_gradient(vfmm_handle h, const void *gamma, double sigma, void *u_out, void *g_out);
+
+/* Adjoint of u = A(x) gamma for a loss L(u) with w = dL/du (device n x 3, caller order), on the
+ * tree of the last vfmm_build_tree (positions frozen):
+ *   dgamma = A^T w = A w   (the Biot-Savart matrix is symmetric: A_ji = A_ij^T),
+ *   dx_m   = (grad u^gamma(x_m))^T w_m + (grad u^w(x_m))^T gamma_m,
+ * where u^w is the velocity induced by strengths w.  With VFMM_METHOD_DIRECT this is the exact
+ * gradient of the evaluated sum; with the FMM, dgamma applies the FMM operator to w, which
+ * equals the transpose of the FMM operator to the FMM's accuracy.  v (dL/dS) must be NULL
+ * (VFMM_ERR_UNSUPPORTED otherwise).  dgamma, dx: device n x 3.  Uses handle-owned temporaries
+ * of 21 n values. */
+int vfmm_eval_adjoint(vfmm_handle h, const void *gamma, double sigma, const void *w, const void *v, void *dgamma,
+                      void *dx);
+
 /* End to end from HOST memory: copies x and gamma to the device, builds the tree,
  * evaluates, copies u and S back, and synchronises.  Pointers are host n x 3 arrays of the
  * configured dtype; s_out may be NULL. */

@@ -8,7 +8,8 @@ import math
 from . import _native
 from ._native import (VfmmError, vfmm_create, vfmm_destroy, vfmm_build_tree,  # noqa: F401
                       vfmm_eval_velocity_stretching, vfmm_eval_host, vfmm_sync,
-                      vfmm_get_timings, vfmm_get_tree_info, vfmm_set_stream, config_default)
+                      vfmm_get_timings, vfmm_get_tree_info, vfmm_set_stream, config_default,
+                      vfmm_eval_velocity_gradient, vfmm_eval_adjoint)
 
 PRECISIONS = {"fp32": _native.VFMM_M2L_FP32, "fp64": _native.VFMM_M2L_FP64,
               "tf32x3": _native.VFMM_M2L_TF32X3, "bf16x3": _native.VFMM_M2L_BF16X3}
@@ -85,6 +86,27 @@ class VortexFMM:
                                       s.data_ptr() if s is not None else 0)
         return u, s
 
+    def eval_gradient(self, gamma, sigma):
+        """Velocity (n, 3) and velocity gradient G (n, 3, 3), G[i, a, k] = du_a/dx_k."""
+        self._check(gamma)
+        torch = self.torch
+        u = torch.empty_like(gamma)
+        g = torch.empty(gamma.shape[0], 3, 3, dtype=gamma.dtype, device=gamma.device)
+        vfmm_set_stream(self.h, torch.cuda.current_stream().cuda_stream)
+        vfmm_eval_velocity_gradient(self.h, gamma.data_ptr(), sigma, u.data_ptr(), g.data_ptr())
+        return u, g
+
+    def adjoint(self, gamma, sigma, w):
+        """(dL/dgamma, dL/dx) for dL/du = w on the current tree."""
+        self._check(gamma)
+        self._check(w)
+        torch = self.torch
+        dg = torch.empty_like(gamma)
+        dx = torch.empty_like(gamma)
+        vfmm_set_stream(self.h, torch.cuda.current_stream().cuda_stream)
+        vfmm_eval_adjoint(self.h, gamma.data_ptr(), sigma, w.data_ptr(), 0, dg.data_ptr(), dx.data_ptr())
+        return dg, dx
+
     def __call__(self, x, gamma, sigma, stretching=True):
         self.build_tree(x)
         return self.eval(gamma, sigma, stretching)
@@ -111,3 +133,47 @@ class VortexFMM:
         vfmm_eval_host(self.h, x.shape[0], x.ctypes.data, gamma.ctypes.data, sigma,
                        u.ctypes.data, s.ctypes.data)
         return u, s
+
+
+def _autograd_function():
+    import torch
+
+    class BiotSavart(torch.autograd.Function):
+        """u, S = (Biot-Savart velocity, stretching) of (x, gamma); differentiable in u.
+
+        backward uses vfmm_eval_adjoint on the tree of the forward positions."""
+
+        @staticmethod
+        def forward(ctx, x, gamma, fmm, sigma):
+            x = x.detach().contiguous()
+            gamma = gamma.detach().contiguous()
+            fmm.build_tree(x)
+            u, s = fmm.eval(gamma, sigma)
+            ctx.save_for_backward(x, gamma)
+            ctx.fmm = fmm
+            ctx.sigma = sigma
+            ctx.mark_non_differentiable(s)
+            return u, s
+
+        @staticmethod
+        def backward(ctx, gu, gs):
+            x, gamma = ctx.saved_tensors
+            if gs is not None and bool((gs != 0).any()):
+                raise NotImplementedError("the stretching output is not differentiable")
+            fmm = ctx.fmm
+            fmm.build_tree(x)
+            dgamma, dx = fmm.adjoint(gamma, ctx.sigma, gu.contiguous())
+            return dx, dgamma, None, None
+
+    return BiotSavart
+
+
+_BS = None
+
+
+def biot_savart(x, gamma, fmm, sigma):
+    """Differentiable (u, S) of particles x with strengths gamma through the handle ``fmm``."""
+    global _BS
+    if _BS is None:
+        _BS = _autograd_function()
+    return _BS.apply(x, gamma, fmm, sigma)

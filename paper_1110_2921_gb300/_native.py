@@ -62,6 +62,8 @@ def lib():
             "vfmm_build_tree": ([H, ctypes.c_int64, V], ctypes.c_int),
             "vfmm_eval_velocity_stretching": ([H, V, ctypes.c_double, V, V], ctypes.c_int),
             "vfmm_eval_host": ([H, ctypes.c_int64, V, V, ctypes.c_double, V, V], ctypes.c_int),
+            "vfmm_eval_velocity_gradient": ([H, V, ctypes.c_double, V, V], ctypes.c_int),
+            "vfmm_eval_adjoint": ([H, V, ctypes.c_double, V, V, V, V], ctypes.c_int),
             "vfmm_sync": ([H], ctypes.c_int),
             "vfmm_get_timings": ([H, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
             "vfmm_get_tree_info": ([H, ctypes.POINTER(ctypes.c_int64), ctypes.c_int], ctypes.c_int),
@@ -117,6 +119,17 @@ def vfmm_eval_velocity_stretching(h, gamma_ptr, sigma, u_ptr, s_ptr):
                                               ctypes.c_void_p(u_ptr),
                                               ctypes.c_void_p(s_ptr) if s_ptr else None),
           "vfmm_eval_velocity_stretching", h)
+
+
+def vfmm_eval_velocity_gradient(h, gamma_ptr, sigma, u_ptr, g_ptr):
+    check(lib().vfmm_eval_velocity_gradient(h, ctypes.c_void_p(gamma_ptr), float(sigma), ctypes.c_void_p(u_ptr),
+                                            ctypes.c_void_p(g_ptr)), "vfmm_eval_velocity_gradient", h)
+
+
+def vfmm_eval_adjoint(h, gamma_ptr, sigma, w_ptr, v_ptr, dgamma_ptr, dx_ptr):
+    check(lib().vfmm_eval_adjoint(h, ctypes.c_void_p(gamma_ptr), float(sigma), ctypes.c_void_p(w_ptr),
+                                  ctypes.c_void_p(v_ptr) if v_ptr else None, ctypes.c_void_p(dgamma_ptr),
+                                  ctypes.c_void_p(dx_ptr)), "vfmm_eval_adjoint", h)
 
 
 def vfmm_eval_host(h, n, x_ptr, gamma_ptr, sigma, u_ptr, s_ptr):

@@ -224,7 +224,7 @@ int check_device_error(Ctx *c)
     return VFMM_OK;
 }
 
-int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out)
+int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out, bool grad = false)
 {
     if (!c->built) return fail(c, VFMM_ERR_NOT_BUILT, "vfmm_build_tree has not been called");
     if (!gamma || !u_out) return fail(c, VFMM_ERR_ARG, "null gamma or u_out");
@@ -324,14 +324,18 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out)
             if ((rc = launch_gemm(c, gp, 8, (int64_t)1 << (3 * (l - 1))))) return rc;
         }
         cudaEventRecord(c->ev[7], st);
-        if ((rc = launch_l2p(c))) return rc;
+        if ((rc = launch_l2p(c, grad))) return rc;
         uf = c->ufar.p;
-        sf = c->sfar.p;
+        sf = grad ? c->gfar.p : c->sfar.p;
     } else {
         for (int k = 3; k <= 7; ++k) cudaEventRecord(c->ev[k], st);
     }
     cudaEventRecord(c->ev[8], st);
-    if ((rc = launch_p2p(c, R, sigma, uf, sf, u_out, s_out, fmm ? -1 : c->cfg.direct_images))) return rc;
+    if (grad) {
+        if ((rc = launch_p2p_grad(c, R, sigma, uf, sf, u_out, s_out, fmm ? -1 : c->cfg.direct_images))) return rc;
+    } else {
+        if ((rc = launch_p2p(c, R, sigma, uf, sf, u_out, s_out, fmm ? -1 : c->cfg.direct_images))) return rc;
+    }
     cudaEventRecord(c->ev[9], st);
     c->timed_eval = true;
     return VFMM_OK;
@@ -489,7 +493,7 @@ int vfmm_destroy(vfmm_handle h)
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->xs, &c->gs, &c->perm, &c->keys, &c->leaf_start, &c->counts, &c->fill, &c->tmpidx,
                       &c->scan_part, &c->err, &c->maxleaf, &c->bbox, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->ufar,
-                      &c->sfar, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->m2m_f64,
+                      &c->sfar, &c->gfar, &c->adj_u, &c->adj_g1, &c->adj_g2, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->m2m_f64,
                       &c->lattice_f64, &c->root_m, &c->kblocks, &c->hx, &c->hg, &c->hu, &c->hs};
     for (DevBuf *b : bufs) release(*b);
     if (c->have_events)
@@ -516,6 +520,37 @@ int vfmm_eval_velocity_stretching(vfmm_handle h, const void *gamma, double sigma
 {
     if (!h) return VFMM_ERR_ARG;
     return eval_impl(&h->c, gamma, sigma, u_out, s_out);
+}
+
+int vfmm_eval_velocity_gradient(vfmm_handle h, const void *gamma, double sigma, void *u_out, void *g_out)
+{
+    if (!h) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    if (!g_out) return fail(c, VFMM_ERR_ARG, "null g_out");
+    if (c->built && c->cfg.method == VFMM_METHOD_FMM) {
+        int st = ensure(c, c->gfar, (size_t)c->n * 9 * c->esz, "far velocity gradient");
+        if (st) return st;
+    }
+    return eval_impl(c, gamma, sigma, u_out, g_out, true);
+}
+
+int vfmm_eval_adjoint(vfmm_handle h, const void *gamma, double sigma, const void *w, const void *v, void *dgamma,
+                      void *dx)
+{
+    if (!h) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    if (v) return fail(c, VFMM_ERR_UNSUPPORTED, "a loss through the stretching term (v != NULL) is not supported");
+    if (!w || !dgamma || !dx || !gamma) return fail(c, VFMM_ERR_ARG, "null argument");
+    if (!c->built) return fail(c, VFMM_ERR_NOT_BUILT, "vfmm_build_tree has not been called");
+    size_t n = (size_t)c->n;
+    int st;
+    if ((st = ensure(c, c->adj_u, n * 3 * c->esz, "adjoint velocity"))) return st;
+    if ((st = ensure(c, c->adj_g1, n * 9 * c->esz, "adjoint gradient"))) return st;
+    if ((st = ensure(c, c->adj_g2, n * 9 * c->esz, "adjoint gradient"))) return st;
+    // grad u of the gamma field, then velocity and grad u of the w field (dL/dgamma = A w)
+    if ((st = vfmm_eval_velocity_gradient(h, gamma, sigma, c->adj_u.p, c->adj_g1.p))) return st;
+    if ((st = vfmm_eval_velocity_gradient(h, w, sigma, dgamma, c->adj_g2.p))) return st;
+    return launch_adjoint_combine(c, c->adj_g1.p, w, c->adj_g2.p, gamma, dx);
 }
 
 int vfmm_eval_host(vfmm_handle h, int64_t n, const void *x, const void *gamma, double sigma, void *u_out,

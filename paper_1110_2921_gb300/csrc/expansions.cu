@@ -493,7 +493,8 @@ template <typename T>
 __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__restrict__ xs,
                                                 const typename V4<T>::type *__restrict__ gs,
                                                 const int *__restrict__ ls, int nside, int log2n, T w, int p, int pc,
-                                                const T *__restrict__ Lc, T *__restrict__ ufar, T *__restrict__ sfar)
+                                                const T *__restrict__ Lc, T *__restrict__ ufar, T *__restrict__ sfar,
+                                                T *__restrict__ gfar)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *F = (T *)smem_raw;            // [3][pc]
@@ -626,13 +627,23 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
         ufar[3 * (int64_t)i + 0] = u0;
         ufar[3 * (int64_t)i + 1] = u1;
         ufar[3 * (int64_t)i + 2] = u2;
-        sfar[3 * (int64_t)i + 0] = s2 * S0;
-        sfar[3 * (int64_t)i + 1] = s2 * S1;
-        sfar[3 * (int64_t)i + 2] = s2 * S2;
+        if (sfar) {
+            sfar[3 * (int64_t)i + 0] = s2 * S0;
+            sfar[3 * (int64_t)i + 1] = s2 * S1;
+            sfar[3 * (int64_t)i + 2] = s2 * S2;
+        }
+        if (gfar) {  // velocity gradient du_a/dx_k = eps_abc d_k d_b psi_c
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gfar[9 * (int64_t)i + 0 + k] = s2 * (Hc(2, k, 1) - Hc(1, k, 2));
+                gfar[9 * (int64_t)i + 3 + k] = s2 * (Hc(0, k, 2) - Hc(2, k, 0));
+                gfar[9 * (int64_t)i + 6 + k] = s2 * (Hc(1, k, 0) - Hc(0, k, 1));
+            }
+        }
     }
 }
 
-int launch_l2p(Ctx *c)
+int launch_l2p(Ctx *c, bool grad)
 {
     int log2n = 0;
     while ((1 << log2n) < c->nside) ++log2n;
@@ -641,12 +652,13 @@ int launch_l2p(Ctx *c)
     if (c->f64)
         k_l2p<double><<<(unsigned)c->nleaf, L2P_BS, sm, c->stream>>>(
             (const dvec4 *)c->xs.p, (const dvec4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,
-            c->leaf_w, c->p, c->pc, (const double *)c->lexp.p + off, (double *)c->ufar.p, (double *)c->sfar.p);
+            c->leaf_w, c->p, c->pc, (const double *)c->lexp.p + off, (double *)c->ufar.p,
+            grad ? nullptr : (double *)c->sfar.p, grad ? (double *)c->gfar.p : nullptr);
     else
         k_l2p<float><<<(unsigned)c->nleaf, L2P_BS, sm, c->stream>>>(
             (const float4 *)c->xs.p, (const float4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,
             (float)c->leaf_w, c->p, c->pc, (const float *)c->lexp.p + off, (float *)c->ufar.p,
-            (float *)c->sfar.p);
+            grad ? nullptr : (float *)c->sfar.p, grad ? (float *)c->gfar.p : nullptr);
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
 }

@@ -612,3 +612,202 @@ extern "C" int vfmm_direct_eval_noalloc(int64_t n, const float *x, const float *
     if (cudaGetLastError() != cudaSuccess) return VFMM_ERR_CUDA;
     return VFMM_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// Velocity gradient at the particles (near field), for the adjoint:
+//   du_a/dx_k = sum_j [ K eps_abk gamma_jb + F (gamma_j x r)_a r_k ]
+// (the derivative of K(r) gamma_j x r; the oracle writes the same sum).
+namespace vfmm {
+
+template <typename T> struct GradAcc {
+    T u[3], A[3], M[9];
+};
+
+template <typename T>
+__device__ __forceinline__ void kernel_KF(T r2, T sigma, T &K, T &F);
+
+template <> __device__ __forceinline__ void kernel_KF<double>(double r2, double sigma, double &K, double &F)
+{
+    const double c = 0.79788456080286535588;
+    double s2 = sigma * sigma, x = r2 / s2;
+    if (x < 0.25) {
+        double kk = 0.0, ff = 0.0, xp = 1.0, xm1 = 1.0, fact = 1.0;
+        for (int q = 0; q < 16; ++q) {
+            double den = fact * (2 * q + 3);
+            kk += (q & 1) ? -xp / den : xp / den;
+            if (q >= 1) ff += (q & 1) ? -2.0 * q * xm1 / den : 2.0 * q * xm1 / den;
+            xm1 = xp;
+            xp *= x;
+            fact *= 2.0 * (q + 1);
+        }
+        K = c / (s2 * sigma) * kk;
+        F = c / (s2 * s2 * sigma) * ff;
+    } else {
+        double r = sqrt(r2), rho = r / sigma, e = exp(-0.5 * x);
+        double q = erf(rho * 0.70710678118654752440) - c * rho * e;
+        K = q / (r2 * r);
+        F = (c * e / (s2 * sigma) - 3.0 * K) / r2;
+    }
+}
+
+template <> __device__ __forceinline__ void kernel_KF<float>(float r2, float sigma, float &K, float &F)
+{
+    const float c = 0.79788456080286535588f;
+    float s2 = sigma * sigma, x = r2 / s2;
+    if (x < 0.25f) {
+        K = c / (s2 * sigma) * series_k<float>(x);
+        F = c / (s2 * s2 * sigma) * series_f<float>(x);
+    } else {
+        float rinv = rsqrt_approx(r2), r = r2 * rinv;
+        float e = ex2_approx(-0.72134752044448170368f * x);  // exp(-x/2) = 2^(-x log2(e)/2)
+        float t = rcp_approx(fmaf(r, 0.3275911f * 0.70710678118654752440f / sigma, 1.0f));
+        float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                              0.254829592f);
+        float q = fmaf(-e, fmaf(c / sigma, r, poly), 1.0f);
+        float rinv2 = rinv * rinv;
+        K = q * rinv2 * rinv;
+        F = rinv2 * (c * e / (s2 * sigma) - 3.0f * K);
+    }
+}
+
+constexpr int PG_BS = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(PG_BS) k_p2p_grad(const typename V4<T>::type *__restrict__ xs,
+                                                    const typename V4<T>::type *__restrict__ gs,
+                                                    const int *__restrict__ ls, int nside, int log2n, int R, int direct_K,
+                                                    T leaf_w, T sigma, T L, const T *__restrict__ ufar,
+                                                    const T *__restrict__ gfar, const int *__restrict__ perm,
+                                                    T *__restrict__ u_out, T *__restrict__ g_out)
+{
+    typedef typename V4<T>::type T4;
+    __shared__ T4 sx[PG_BS];
+    __shared__ T4 sg[PG_BS];
+    const int leaf = blockIdx.x;
+    const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
+    const int tb = ls[leaf], te = ls[leaf + 1];
+    const T zx = (cx + T(0.5)) * leaf_w, zy = (cy + T(0.5)) * leaf_w, zz = (cz + T(0.5)) * leaf_w;
+    for (int t0 = tb + blockIdx.y * PG_BS; t0 < te; t0 += gridDim.y * PG_BS) {
+        const int ti = t0 + threadIdx.x;
+        const bool active = ti < te;
+        T4 xi = active ? xs[ti] : make_v4<T>(zx, zy, zz, T(0));
+        T xi0 = xi.x - zx, xi1 = xi.y - zy, xi2 = xi.z - zz;  // leaf-relative
+        GradAcc<T> a;
+        for (int q = 0; q < 3; ++q) a.u[q] = a.A[q] = 0;
+        for (int q = 0; q < 9; ++q) a.M[q] = 0;
+        int lo[3], hi[3];
+        const int cc[3] = {cx, cy, cz};
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = direct_K >= 0 ? -cc[d] - direct_K * nside : -R;
+            hi[d] = direct_K >= 0 ? nside - 1 - cc[d] + direct_K * nside : R;
+        }
+        for (int ox = lo[0]; ox <= hi[0]; ++ox)
+            for (int oy = lo[1]; oy <= hi[1]; ++oy)
+                for (int oz = lo[2]; oz <= hi[2]; ++oz) {
+                    int nx = cx + ox, ny = cy + oy, nz = cz + oz;
+                    int sl = ((nx & (nside - 1)) * nside + (ny & (nside - 1))) * nside + (nz & (nside - 1));
+                    T o0 = L * (T)(nx >> log2n) - zx, o1 = L * (T)(ny >> log2n) - zy, o2 = L * (T)(nz >> log2n) - zz;
+                    const bool own = ox == 0 && oy == 0 && oz == 0;  // own leaf, primary image: skip j = i
+                    int sb = ls[sl], se = ls[sl + 1];
+                    for (int s0 = sb; s0 < se; s0 += PG_BS) {
+                        int cnt = min(PG_BS, se - s0);
+                        __syncthreads();
+                        if (threadIdx.x < cnt) {
+                            T4 x = xs[s0 + threadIdx.x];
+                            sx[threadIdx.x] = make_v4<T>(x.x + o0, x.y + o1, x.z + o2, T(0));
+                            sg[threadIdx.x] = gs[s0 + threadIdx.x];
+                        }
+                        __syncthreads();
+                        for (int j = 0; j < cnt; ++j) {
+                            if (own && s0 + j == ti) continue;
+                            T4 xj = sx[j], gj = sg[j];
+                            T r0 = xi0 - xj.x, r1 = xi1 - xj.y, r2c = xi2 - xj.z;
+                            T r2 = r0 * r0 + r1 * r1 + r2c * r2c;
+                            T K, F;
+                            kernel_KF<T>(r2, sigma, K, F);
+                            T W0 = gj.y * r2c - gj.z * r1, W1 = gj.z * r0 - gj.x * r2c, W2 = gj.x * r1 - gj.y * r0;
+                            a.u[0] += K * W0;
+                            a.u[1] += K * W1;
+                            a.u[2] += K * W2;
+                            a.A[0] += K * gj.x;
+                            a.A[1] += K * gj.y;
+                            a.A[2] += K * gj.z;
+                            T FW0 = F * W0, FW1 = F * W1, FW2 = F * W2;
+                            a.M[0] += FW0 * r0; a.M[1] += FW0 * r1; a.M[2] += FW0 * r2c;
+                            a.M[3] += FW1 * r0; a.M[4] += FW1 * r1; a.M[5] += FW1 * r2c;
+                            a.M[6] += FW2 * r0; a.M[7] += FW2 * r1; a.M[8] += FW2 * r2c;
+                        }
+                    }
+                }
+        if (!active) continue;
+        const T f = T(0.0795774715459476679);
+        // G_ak = eps_abk A_b + M_ak
+        T G[9];
+        G[0] = a.M[0];
+        G[1] = a.M[1] - a.A[2];
+        G[2] = a.M[2] + a.A[1];
+        G[3] = a.M[3] + a.A[2];
+        G[4] = a.M[4];
+        G[5] = a.M[5] - a.A[0];
+        G[6] = a.M[6] - a.A[1];
+        G[7] = a.M[7] + a.A[0];
+        G[8] = a.M[8];
+        int64_t o = perm[ti];
+        for (int q = 0; q < 3; ++q) u_out[3 * o + q] = f * a.u[q] + (ufar ? ufar[3 * (int64_t)ti + q] : T(0));
+        for (int q = 0; q < 9; ++q) g_out[9 * o + q] = f * G[q] + (gfar ? gfar[9 * (int64_t)ti + q] : T(0));
+    }
+}
+
+int launch_p2p_grad(Ctx *c, int R, double sigma, const void *ufar, const void *gfar, void *u_out, void *g_out,
+                    int direct_K)
+{
+    int log2n = 0;
+    while ((1 << log2n) < c->nside) ++log2n;
+    int chunks = (c->max_leaf + PG_BS - 1) / PG_BS;
+    if (chunks < 1) chunks = 1;
+    if (chunks > 65535) chunks = 65535;
+    dim3 grid((unsigned)c->nleaf, (unsigned)chunks);
+    if (c->f64)
+        k_p2p_grad<double><<<grid, PG_BS, 0, c->stream>>>((const dvec4 *)c->xs.p, (const dvec4 *)c->gs.p,
+                                                         (const int *)c->leaf_start.p, c->nside, log2n, R, direct_K,
+                                                         c->leaf_w, sigma, c->cfg.box, (const double *)ufar,
+                                                         (const double *)gfar, (const int *)c->perm.p,
+                                                         (double *)u_out, (double *)g_out);
+    else
+        k_p2p_grad<float><<<grid, PG_BS, 0, c->stream>>>((const float4 *)c->xs.p, (const float4 *)c->gs.p,
+                                                        (const int *)c->leaf_start.p, c->nside, log2n, R, direct_K,
+                                                        (float)c->leaf_w, (float)sigma, (float)c->cfg.box,
+                                                        (const float *)ufar, (const float *)gfar,
+                                                        (const int *)c->perm.p, (float *)u_out, (float *)g_out);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+// dx_m = G1_m^T w_m + G2_m^T gamma_m (all arrays in caller order)
+template <typename T>
+__global__ void k_adjoint_combine(int64_t n, const T *__restrict__ G1, const T *__restrict__ w,
+                                  const T *__restrict__ G2, const T *__restrict__ g, T *__restrict__ dx)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < 3; ++k) {
+        T s = 0;
+        for (int a = 0; a < 3; ++a) s += G1[9 * i + 3 * a + k] * w[3 * i + a] + G2[9 * i + 3 * a + k] * g[3 * i + a];
+        dx[3 * i + k] = s;
+    }
+}
+
+int launch_adjoint_combine(Ctx *c, const void *G1, const void *w, const void *G2, const void *gamma, void *dx)
+{
+    int nb = (int)((c->n + 255) / 256);
+    if (c->f64)
+        k_adjoint_combine<double><<<nb, 256, 0, c->stream>>>(c->n, (const double *)G1, (const double *)w,
+                                                            (const double *)G2, (const double *)gamma, (double *)dx);
+    else
+        k_adjoint_combine<float><<<nb, 256, 0, c->stream>>>(c->n, (const float *)G1, (const float *)w,
+                                                           (const float *)G2, (const float *)gamma, (float *)dx);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+}  // namespace vfmm

@@ -86,7 +86,8 @@ struct Ctx {
     DevBuf bbox;                   // per leaf: float4 lo, float4 hi of its particles
     DevBuf mexp, lexp;             // all levels, T
     DevBuf mhi, mlo;               // tensor-core copies of the multipoles (largest level)
-    DevBuf ufar, sfar;             // far-field u, S in sorted order, T
+    DevBuf ufar, sfar, gfar;       // far-field u, S (or grad u) in sorted order, T
+    DevBuf adj_u, adj_g1, adj_g2;  // adjoint temporaries (caller order)
     DevBuf at_m2l, at_m2m, at_l2l; // CUDA-core matrices, T
     DevBuf tc_hi, tc_lo;           // tensor-core tiles
     DevBuf m2m_f64, lattice_f64;   // root accumulation and lattice operator, FP64
@@ -113,7 +114,10 @@ int launch_gather_gamma(Ctx *c, const void *gamma);
 int launch_p2m(Ctx *c);
 int launch_gemm(Ctx *c, const GemmParams &gp, int ngroups, int64_t ncell_group);
 int launch_root(Ctx *c);
-int launch_l2p(Ctx *c);
+int launch_l2p(Ctx *c, bool grad);
+int launch_p2p_grad(Ctx *c, int R, double sigma, const void *ufar, const void *gfar, void *u_out, void *g_out,
+                    int direct_K);
+int launch_adjoint_combine(Ctx *c, const void *G1, const void *w, const void *G2, const void *gamma, void *dx);
 // direct_K >= 0: direct sum over every leaf of the (2K+1)^3 image boxes; -1: the FMM near field (R rings)
 int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, void *u_out,
                void *s_out, int direct_K);
