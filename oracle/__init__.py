@@ -11,6 +11,8 @@ Contents
   Section 4.1.  Optional full velocity gradient.
 * ``spectral``: the fully periodic field as a Fourier series (independent of the direct sum).
 * ``gradient``: dL/dgamma and dL/dx of L = sum |u - u*|^2 from the direct sums.
+* ``integrate``: one Heun step of Eqs. (convection), (stretching), (csm); FP64 diagnostics.
+* ``reinit``: Gaussian-basis reinitialisation onto a lattice (dense FP64, small lattices).
 
 Parity status: every function here is pinned by the ``tests/test_oracle_*.py`` checks
 (closed forms, quadrature, mpmath brute force, invariants, spectral cross-check).
@@ -98,3 +100,5 @@ def direct(x, gamma, sigma, L=2 * np.pi, K=1, targets=None, kmin=0, grad=False,
 
 from . import spectral  # noqa: E402,F401
 from . import gradient  # noqa: E402,F401
+from . import integrate  # noqa: E402,F401
+from . import reinit  # noqa: E402,F401

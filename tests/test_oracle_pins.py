@@ -289,3 +289,69 @@ def test_loss_gradient_matches_central_differences():
         xm[i, a] -= eps
         fd = (oracle.gradient.loss(xp, g, sigma, ustar) - oracle.gradient.loss(xm, g, sigma, ustar)) / (2 * eps)
         assert abs(fd - dx[i, a]) < 1e-7 * max(1.0, abs(fd)), (i, a, fd, dx[i, a])
+
+
+def test_heun_step_is_second_order():
+    # Heun's global error falls 4x per halving of dt (a first-order bug would give 2x)
+    n = 3
+    h = 2 * np.pi / n
+    x0 = wl.jitter(wl.lattice_positions(n), h, 0.2, seed=31)
+    g0 = np.random.default_rng(32).normal(size=x0.shape) * 0.5
+    sigma, nu, T = 0.9 * h, 0.01, 0.4
+
+    def run(nsteps):
+        x, g, s = x0.copy(), g0.copy(), sigma
+        dt = T / nsteps
+        for _ in range(nsteps):
+            x, g, s = oracle.integrate.heun_step(x, g, s, dt, nu, K=0)
+        return x, g, s
+
+    xr, gr, sr = run(64)
+    errs = []
+    for m in (4, 8, 16):
+        x, g, s = run(m)
+        assert abs(s - sr) < 1e-12   # core spreading is exact: sigma^2 = sigma0^2 + 2 nu t
+        d = np.mod(x - xr + np.pi, 2 * np.pi) - np.pi
+        errs.append(np.abs(d).max() + np.abs(g - gr).max())
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0, errs
+
+
+def test_gaussian_basis_is_normalised():
+    # Eq. (gaussian): zeta integrates to one (lattice quadrature of a well-resolved core)
+    n = 24
+    h = 2 * np.pi / n
+    xl = wl.lattice_positions(n)
+    src = np.array([[np.pi, np.pi, np.pi]])
+    w = oracle.reinit.gaussian_sum(xl, src, np.array([[1.0, 0.0, 0.0]]), 2.0 * h)
+    assert abs(w[:, 0].sum() * h ** 3 - 1.0) < 1e-10
+
+
+def test_reinit_deconvolves_a_single_gaussian():
+    # one old particle of core sigma = 2h on a new lattice point, new core sigma0 = h: since
+    # zeta_a * zeta_b = zeta_sqrt(a^2 + b^2), Z gamma' = omega is solved by lattice samples of a
+    # Gaussian of width sqrt(sigma^2 - sigma0^2) (with its periodic images), times h^3
+    import itertools
+    m = 12
+    h = 2 * np.pi / m
+    xl = wl.lattice_positions(m)
+    j = 400
+    gj = np.array([[0.3, -0.5, 0.8]])
+    sigma = 2.0 * h
+    w = np.sqrt(sigma ** 2 - h ** 2)
+    exact = np.zeros((len(xl), 1))
+    for nimg in itertools.product((-1, 0, 1), repeat=3):
+        d = xl - xl[j] - np.array(nimg) * 2 * np.pi
+        exact[:, 0] += np.exp(-0.5 * (d * d).sum(1) / w ** 2) / (2 * np.pi * w * w) ** 1.5
+    exact = exact * gj * h ** 3
+    _, g, res, _ = oracle.reinit.reinit(xl[j:j + 1], gj, sigma, m, iters=300)
+    assert res < 2e-5
+    assert np.linalg.norm(g - exact) < 5e-4 * np.linalg.norm(exact)
+
+
+def test_reinit_residual_decreases():
+    m = 6
+    h = 2 * np.pi / m
+    x = wl.jitter(wl.lattice_positions(m), h, 0.3, seed=51)
+    g = np.random.default_rng(52).normal(size=x.shape) * h ** 3
+    res = [oracle.reinit.reinit(x, g, 1.1 * h, m, iters=k)[2] for k in (0, 1, 5, 20)]
+    assert res[0] > res[1] > res[2] > res[3]
