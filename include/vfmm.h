@@ -134,6 +134,33 @@ int vfmm_eval_velocity_gradient(vfmm_handle h, const void *gamma, double sigma, 
 int vfmm_eval_adjoint(vfmm_handle h, const void *gamma, double sigma, const void *w, const void *v, void *dgamma,
                       void *dx);
 
+/* One time step of the vortex method (Section 2.2: Eqs. convection, stretching, csm) by the
+ * explicit trapezoid (Heun) rule: (u1, S1) at (x, gamma, sigma); (u2, S2) at
+ * (x + dt u1, gamma + dt S1, sqrt(sigma^2 + 2 nu dt)); then x += dt (u1 + u2)/2 wrapped into
+ * [0, L), gamma += dt (S1 + S2)/2, sigma^2 += 2 nu dt (core spreading, exact).  x, gamma: device
+ * n x 3 (caller order), updated in place; sigma: host, updated.  Builds the tree twice; the
+ * handle's tree is stale afterwards (call vfmm_build_tree before the next evaluation).
+ * Errors: n <= 0, NULL pointers, non-finite dt or nu, nu < 0, sigma <= 0 -> VFMM_ERR_ARG. */
+int vfmm_rk_step(vfmm_handle h, int64_t n, void *x, void *gamma, double *sigma, double dt, double nu);
+
+/* Reinitialise n particles (x, gamma, core sigma; device n x 3, caller order) onto the m^3
+ * cell-centre lattice of [0, L)^3 with core sigma_new (<= 0: the lattice spacing h = L/m)
+ * (Section 2.2, RBF interpolation): omega(x_g) = sum_j gamma_j zeta_sigma(x_g - x_j) with the
+ * Gaussian basis of Eq. (gaussian), then iters steepest-descent steps with exact line search
+ * on 0.5 |Z gamma' - omega|^2, Z_gk = zeta_sigma_new(x_g - x_k), from gamma' = omega h^3
+ * (Section 5.3).  x_new, gamma_new: device m^3 x 3 outputs, lattice order (ix m + iy) m + iz.
+ * residual (host, may be NULL): |omega - Z gamma'| / |omega|.  Gaussians are cut at 6 sigma.
+ * Synchronises the stream; the handle's tree is stale afterwards.
+ * Errors: bad sizes or non-finite sigma -> VFMM_ERR_ARG; a lattice finer than 64 points per
+ * leaf side or more than 32 stencil taps -> VFMM_ERR_UNSUPPORTED. */
+int vfmm_reinit(vfmm_handle h, int64_t n, const void *x, const void *gamma, double sigma, int m, double sigma_new,
+                int iters, void *x_new, void *gamma_new, double *residual);
+
+/* FP64 sums over n particles (device arrays; u may be NULL): out[0..2] = sum gamma (total
+ * vorticity), out[3..5] = sum x cross gamma (twice the linear impulse), out[6] = sum |u|^2,
+ * out[7] = sum |gamma|^2.  Synchronises the stream. */
+int vfmm_diagnostics(vfmm_handle h, int64_t n, const void *x, const void *gamma, const void *u, double *out);
+
 /* End to end from HOST memory: copies x and gamma to the device, builds the tree,
  * evaluates, copies u and S back, and synchronises.  Pointers are host n x 3 arrays of the
  * configured dtype; s_out may be NULL. */

@@ -9,7 +9,8 @@ from . import _native
 from ._native import (VfmmError, vfmm_create, vfmm_destroy, vfmm_build_tree,  # noqa: F401
                       vfmm_eval_velocity_stretching, vfmm_eval_host, vfmm_sync,
                       vfmm_get_timings, vfmm_get_tree_info, vfmm_set_stream, config_default,
-                      vfmm_eval_velocity_gradient, vfmm_eval_adjoint)
+                      vfmm_eval_velocity_gradient, vfmm_eval_adjoint, vfmm_rk_step, vfmm_diagnostics,
+                      vfmm_reinit)
 
 PRECISIONS = {"fp32": _native.VFMM_M2L_FP32, "fp64": _native.VFMM_M2L_FP64,
               "tf32x3": _native.VFMM_M2L_TF32X3, "bf16x3": _native.VFMM_M2L_BF16X3}
@@ -106,6 +107,34 @@ class VortexFMM:
         vfmm_set_stream(self.h, torch.cuda.current_stream().cuda_stream)
         vfmm_eval_adjoint(self.h, gamma.data_ptr(), sigma, w.data_ptr(), 0, dg.data_ptr(), dx.data_ptr())
         return dg, dx
+
+    def rk_step(self, x, gamma, sigma, dt, nu):
+        """One Heun step in place on x, gamma; returns the new core size."""
+        self._check(x)
+        self._check(gamma)
+        vfmm_set_stream(self.h, self.torch.cuda.current_stream().cuda_stream)
+        s = vfmm_rk_step(self.h, x.shape[0], x.data_ptr(), gamma.data_ptr(), sigma, dt, nu)
+        self.n = 0
+        return s
+
+    def reinit(self, x, gamma, sigma, m, sigma_new=0.0, iters=20):
+        """New particles on the m^3 lattice: (x_new, gamma_new, residual)."""
+        self._check(x)
+        self._check(gamma)
+        torch = self.torch
+        xn = torch.empty(m ** 3, 3, dtype=x.dtype, device=x.device)
+        gn = torch.empty_like(xn)
+        vfmm_set_stream(self.h, torch.cuda.current_stream().cuda_stream)
+        res = vfmm_reinit(self.h, x.shape[0], x.data_ptr(), gamma.data_ptr(), sigma, m, sigma_new, iters,
+                          xn.data_ptr(), gn.data_ptr())
+        self.n = 0
+        return xn, gn, res
+
+    def diagnostics(self, x, gamma, u=None):
+        """FP64 total vorticity, sum x cross gamma, sum |u|^2, sum |gamma|^2."""
+        vfmm_set_stream(self.h, self.torch.cuda.current_stream().cuda_stream)
+        v = vfmm_diagnostics(self.h, x.shape[0], x.data_ptr(), gamma.data_ptr(), u.data_ptr() if u is not None else 0)
+        return {"total_vorticity": v[0:3], "x_cross_gamma": v[3:6], "sum_u2": v[6], "sum_gamma2": v[7]}
 
     def __call__(self, x, gamma, sigma, stretching=True):
         self.build_tree(x)

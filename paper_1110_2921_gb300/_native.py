@@ -64,6 +64,11 @@ def lib():
             "vfmm_eval_host": ([H, ctypes.c_int64, V, V, ctypes.c_double, V, V], ctypes.c_int),
             "vfmm_eval_velocity_gradient": ([H, V, ctypes.c_double, V, V], ctypes.c_int),
             "vfmm_eval_adjoint": ([H, V, ctypes.c_double, V, V, V, V], ctypes.c_int),
+            "vfmm_rk_step": ([H, ctypes.c_int64, V, V, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                              ctypes.c_double], ctypes.c_int),
+            "vfmm_diagnostics": ([H, ctypes.c_int64, V, V, V, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "vfmm_reinit": ([H, ctypes.c_int64, V, V, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                             V, V, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "vfmm_sync": ([H], ctypes.c_int),
             "vfmm_get_timings": ([H, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
             "vfmm_get_tree_info": ([H, ctypes.POINTER(ctypes.c_int64), ctypes.c_int], ctypes.c_int),
@@ -130,6 +135,28 @@ def vfmm_eval_adjoint(h, gamma_ptr, sigma, w_ptr, v_ptr, dgamma_ptr, dx_ptr):
     check(lib().vfmm_eval_adjoint(h, ctypes.c_void_p(gamma_ptr), float(sigma), ctypes.c_void_p(w_ptr),
                                   ctypes.c_void_p(v_ptr) if v_ptr else None, ctypes.c_void_p(dgamma_ptr),
                                   ctypes.c_void_p(dx_ptr)), "vfmm_eval_adjoint", h)
+
+
+def vfmm_rk_step(h, n, x_ptr, gamma_ptr, sigma, dt, nu):
+    s = ctypes.c_double(sigma)
+    check(lib().vfmm_rk_step(h, int(n), ctypes.c_void_p(x_ptr), ctypes.c_void_p(gamma_ptr), ctypes.byref(s),
+                             float(dt), float(nu)), "vfmm_rk_step", h)
+    return s.value
+
+
+def vfmm_reinit(h, n, x_ptr, gamma_ptr, sigma, m, sigma_new, iters, x_new_ptr, gamma_new_ptr):
+    res = ctypes.c_double(0.0)
+    check(lib().vfmm_reinit(h, int(n), ctypes.c_void_p(x_ptr), ctypes.c_void_p(gamma_ptr), float(sigma), int(m),
+                            float(sigma_new), int(iters), ctypes.c_void_p(x_new_ptr), ctypes.c_void_p(gamma_new_ptr),
+                            ctypes.byref(res)), "vfmm_reinit", h)
+    return res.value
+
+
+def vfmm_diagnostics(h, n, x_ptr, gamma_ptr, u_ptr):
+    out = (ctypes.c_double * 8)()
+    check(lib().vfmm_diagnostics(h, int(n), ctypes.c_void_p(x_ptr), ctypes.c_void_p(gamma_ptr),
+                                 ctypes.c_void_p(u_ptr) if u_ptr else None, out), "vfmm_diagnostics", h)
+    return list(out)
 
 
 def vfmm_eval_host(h, n, x_ptr, gamma_ptr, sigma, u_ptr, s_ptr):

@@ -347,7 +347,9 @@ int build_impl(Ctx *c, int64_t n, const void *x)
     if (n > (int64_t)1 << 30) return fail(c, VFMM_ERR_UNSUPPORTED, "n above 2^30 particles");
     if (!x) return fail(c, VFMM_ERR_ARG, "null x");
     int D;
-    if (c->cfg.depth > 0) {
+    if (c->depth_override >= 0) {
+        D = c->depth_override;
+    } else if (c->cfg.depth > 0) {
         D = c->cfg.depth;
     } else {
         double ratio = (double)n / (double)(c->cfg.ncrit > 0 ? c->cfg.ncrit : 64);
@@ -493,7 +495,7 @@ int vfmm_destroy(vfmm_handle h)
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->xs, &c->gs, &c->perm, &c->keys, &c->leaf_start, &c->counts, &c->fill, &c->tmpidx,
                       &c->scan_part, &c->err, &c->maxleaf, &c->bbox, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->ufar,
-                      &c->sfar, &c->gfar, &c->adj_u, &c->adj_g1, &c->adj_g2, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->m2m_f64,
+                      &c->sfar, &c->gfar, &c->adj_u, &c->adj_g1, &c->adj_g2, &c->rk_u1, &c->rk_s1, &c->rk_u2, &c->rk_s2, &c->rk_x1, &c->rk_g1, &c->diag, &c->rg_om, &c->rg_r, &c->rg_d, &c->rg_q, &c->rg_t1, &c->rg_t2, &c->rg_dots, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->m2m_f64,
                       &c->lattice_f64, &c->root_m, &c->kblocks, &c->hx, &c->hg, &c->hu, &c->hs};
     for (DevBuf *b : bufs) release(*b);
     if (c->have_events)
@@ -551,6 +553,88 @@ int vfmm_eval_adjoint(vfmm_handle h, const void *gamma, double sigma, const void
     if ((st = vfmm_eval_velocity_gradient(h, gamma, sigma, c->adj_u.p, c->adj_g1.p))) return st;
     if ((st = vfmm_eval_velocity_gradient(h, w, sigma, dgamma, c->adj_g2.p))) return st;
     return launch_adjoint_combine(c, c->adj_g1.p, w, c->adj_g2.p, gamma, dx);
+}
+
+int vfmm_rk_step(vfmm_handle h, int64_t n, void *x, void *gamma, double *sigma, double dt, double nu)
+{
+    if (!h) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    if (n <= 0 || !x || !gamma || !sigma) return fail(c, VFMM_ERR_ARG, "bad arguments");
+    if (!std::isfinite(dt) || !std::isfinite(nu) || nu < 0.0) return fail(c, VFMM_ERR_ARG, "dt and nu must be finite, nu >= 0");
+    const double s0 = *sigma;
+    if (!std::isfinite(s0) || s0 <= 0.0) return fail(c, VFMM_ERR_ARG, "sigma must be finite and > 0");
+    const double s1sq = s0 * s0 + 2.0 * nu * dt;
+    if (!(s1sq > 0.0)) return fail(c, VFMM_ERR_ARG, "sigma^2 + 2 nu dt must be > 0");
+    const double s1 = std::sqrt(s1sq);
+    const size_t bytes = (size_t)n * 3 * c->esz;
+    int st;
+    DevBuf *tmp[] = {&c->rk_u1, &c->rk_s1, &c->rk_u2, &c->rk_s2, &c->rk_x1, &c->rk_g1};
+    for (DevBuf *b : tmp)
+        if ((st = ensure(c, *b, bytes, "time-step temporaries"))) return st;
+    const double L = c->cfg.box;
+    // stage 1 at (x, gamma, sigma)
+    if ((st = build_impl(c, n, x))) return st;
+    if ((st = eval_impl(c, gamma, s0, c->rk_u1.p, c->rk_s1.p))) return st;
+    if ((st = launch_axpy3(c, n, x, c->rk_u1.p, nullptr, dt, L, c->rk_x1.p))) return st;
+    if ((st = launch_axpy3(c, n, gamma, c->rk_s1.p, nullptr, dt, 0.0, c->rk_g1.p))) return st;
+    // stage 2 at (x + dt u1, gamma + dt S1, sqrt(sigma^2 + 2 nu dt))
+    if ((st = build_impl(c, n, c->rk_x1.p))) return st;
+    if ((st = eval_impl(c, c->rk_g1.p, s1, c->rk_u2.p, c->rk_s2.p))) return st;
+    if ((st = launch_axpy3(c, n, x, c->rk_u1.p, c->rk_u2.p, 0.5 * dt, L, x))) return st;
+    if ((st = launch_axpy3(c, n, gamma, c->rk_s1.p, c->rk_s2.p, 0.5 * dt, 0.0, gamma))) return st;
+    *sigma = s1;
+    c->built = false;  // the tree holds the stage-2 positions
+    return VFMM_OK;
+}
+
+int vfmm_reinit(vfmm_handle h, int64_t n, const void *x, const void *gamma, double sigma, int m, double sigma_new,
+                int iters, void *x_new, void *gamma_new, double *residual)
+{
+    if (!h) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    if (n <= 0 || !x || !gamma || !x_new || !gamma_new) return fail(c, VFMM_ERR_ARG, "bad arguments");
+    if (m < 2 || (int64_t)m * m * m > ((int64_t)1 << 30)) return fail(c, VFMM_ERR_ARG, "lattice size m out of range");
+    if (iters < 0 || iters > 100000) return fail(c, VFMM_ERR_ARG, "iters out of range");
+    if (!std::isfinite(sigma) || sigma <= 0.0) return fail(c, VFMM_ERR_ARG, "sigma must be finite and > 0");
+    const double hl = c->cfg.box / m;
+    if (!(sigma_new > 0.0)) sigma_new = hl;
+    if (!std::isfinite(sigma_new)) return fail(c, VFMM_ERR_ARG, "sigma_new must be finite");
+    // octree of the old particles with leaves aligned to the new lattice (m divisible by 2^D)
+    double ratio = (double)n / (double)(c->cfg.ncrit > 0 ? c->cfg.ncrit : 64);
+    int D = (int)std::lround(std::log(ratio > 1.0 ? ratio : 1.0) / std::log(8.0));
+    if (D > MAX_DEPTH) D = MAX_DEPTH;
+    while (D > 0 && (m % (1 << D)) != 0) --D;
+    if ((m >> D) > 64) return fail(c, VFMM_ERR_UNSUPPORTED, "lattice too fine for the particle tree");
+    c->depth_override = D;
+    int st = build_impl(c, n, x);
+    c->depth_override = -1;
+    if (st) return st;
+    if ((st = launch_gather_gamma(c, gamma))) return st;
+    int R = (int)std::ceil(6.0 * sigma / c->leaf_w);
+    if (R < 1) R = 1;
+    const size_t bytes = (size_t)m * m * m * 3 * c->esz;
+    DevBuf *tmp[] = {&c->rg_om, &c->rg_r, &c->rg_d, &c->rg_q, &c->rg_t1, &c->rg_t2};
+    for (DevBuf *b : tmp)
+        if ((st = ensure(c, *b, bytes, "reinitialisation temporaries"))) return st;
+    if ((st = ensure(c, c->rg_dots, 4 * sizeof(double), "reinitialisation sums"))) return st;
+    st = launch_reinit(c, m, sigma, sigma_new, iters, R, x_new, gamma_new, residual);
+    c->built = false;  // the tree holds the old particles
+    return st;
+}
+
+int vfmm_diagnostics(vfmm_handle h, int64_t n, const void *x, const void *gamma, const void *u, double *out)
+{
+    if (!h) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    if (n <= 0 || !x || !gamma || !out) return fail(c, VFMM_ERR_ARG, "bad arguments");
+    int st;
+    if ((st = ensure(c, c->diag, 8 * sizeof(double), "diagnostics"))) return st;
+    cudaMemsetAsync(c->diag.p, 0, 8 * sizeof(double), c->stream);
+    if ((st = launch_diag(c, n, x, gamma, u, (double *)c->diag.p))) return st;
+    cudaError_t e = cudaMemcpyAsync(out, c->diag.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics");
+    return VFMM_OK;
 }
 
 int vfmm_eval_host(vfmm_handle h, int64_t n, const void *x, const void *gamma, double sigma, void *u_out,

@@ -88,6 +88,10 @@ struct Ctx {
     DevBuf mhi, mlo;               // tensor-core copies of the multipoles (largest level)
     DevBuf ufar, sfar, gfar;       // far-field u, S (or grad u) in sorted order, T
     DevBuf adj_u, adj_g1, adj_g2;  // adjoint temporaries (caller order)
+    DevBuf rk_u1, rk_s1, rk_u2, rk_s2, rk_x1, rk_g1;  // time-step temporaries (caller order)
+    DevBuf diag;                   // 8 FP64 sums
+    DevBuf rg_om, rg_r, rg_d, rg_q, rg_t1, rg_t2, rg_dots;  // reinitialisation temporaries
+    int depth_override = -1;       // tree depth forced by vfmm_reinit
     DevBuf at_m2l, at_m2m, at_l2l; // CUDA-core matrices, T
     DevBuf tc_hi, tc_lo;           // tensor-core tiles
     DevBuf m2m_f64, lattice_f64;   // root accumulation and lattice operator, FP64
@@ -124,5 +128,9 @@ int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, 
 int launch_tc_m2l(Ctx *c, int level, const int4 *kb_dev, const int *kb_off, const int *kb_cnt, bool bf16);
 int launch_split(Ctx *c, int level, bool bf16);
 void set_constants(int p);
+int launch_axpy3(Ctx *c, int64_t n, const void *a, const void *b, const void *d, double coef, double wrap_L, void *out);
+int launch_diag(Ctx *c, int64_t n, const void *x, const void *g, const void *u, double *out_dev);
+int launch_reinit(Ctx *c, int m, double sigma, double sigma0, int iters, int R, void *x_new, void *g_new,
+                  double *residual);
 
 }  // namespace vfmm
