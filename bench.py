@@ -104,6 +104,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def combine_ranks(ms, particles, steps, device=None):
+    """Max-over-ranks time (ms) and whole-job particles/s.
+
+    Replicas: every rank evaluates its own field of ``particles`` particles, so the job
+    processes world_size * particles * steps particles in the slowest rank's time."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, ws * particles * steps / (ms_max / 1e3)
+
+
 def p2p_work(x, L, depth, R, sigma):
     """Pairs the P2P visits, split as the kernel splits them by leaf-box separation d:
     d < 6.5 sigma -> smoothed kernel (61 flops), d >= 6.5 sigma -> singular kernel (42 flops).
@@ -284,11 +299,7 @@ def main():
         torch.distributed.barrier()
     ms = t0.elapsed_time(t1)
     clk = clocks.stop() if clocks else None
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t_max.item())
-    value = ws * N * args.steps / (ms_max / 1e3)
+    ms_max, value = combine_ranks(ms, N, args.steps, device=dev)
 
     # end to end from pinned host memory through vfmm_eval_host (H2D x, gamma; D2H u, S)
     xh = torch.tensor(f["x"], dtype=torch.float32).pin_memory()
@@ -306,10 +317,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
-    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = ws * N / (float(e2e_t.item()) / 1e3)
+    _, e2e_value = combine_ranks(e2e_ms, N, 1, device=dev)
     if rank != 0:
         if ws > 1:
             torch.distributed.barrier()
