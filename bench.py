@@ -120,28 +120,39 @@ def combine_ranks(ms, particles, steps, device=None):
 
 
 def p2p_work(x, L, depth, R, sigma):
-    """Pairs the P2P visits, split as the kernel splits them by leaf-box separation d:
-    d < 6.5 sigma -> smoothed kernel (61 flops), d >= 6.5 sigma -> singular kernel (42 flops).
-    Returns (pairs, flops)."""
+    """Pairs the P2P visits, split as the kernel splits them: by the gap d between the target
+    leaf's box and each source octant's box, d < 6.5 sigma -> smoothed kernel (61 flops),
+    d >= 6.5 sigma -> singular kernel (42 flops).  Returns (pairs, flops)."""
     import itertools
     import numpy as np
     ns = 1 << depth
     xf = np.mod(x, L).astype(np.float32).astype(np.float64)
     c = np.clip((xf / L * ns).astype(np.int64), 0, ns - 1)
+    o = np.clip((xf / L * 2 * ns).astype(np.int64) - 2 * c, 0, 1)
     key = (c[:, 0] * ns + c[:, 1]) * ns + c[:, 2]
+    okey = key * 8 + (o[:, 0] * 4 + o[:, 1] * 2 + o[:, 2])
     nleaf = ns ** 3
-    cnt = np.bincount(key, minlength=nleaf).astype(np.float64)
-    lo = np.full((nleaf, 3), 3e38)
-    hi = np.full((nleaf, 3), -3e38)
-    order = np.argsort(key, kind="stable")
-    xs = xf[order]
-    ne = cnt > 0
-    starts = np.concatenate([[0], np.cumsum(cnt)[:-1]]).astype(np.int64)[ne]
-    lo[ne] = np.minimum.reduceat(xs, starts, axis=0)
-    hi[ne] = np.maximum.reduceat(xs, starts, axis=0)
+
+    def boxes(k, nk):
+        cnt = np.bincount(k, minlength=nk).astype(np.float64)
+        lo = np.full((nk, 3), 3e38)
+        hi = np.full((nk, 3), -3e38)
+        order = np.argsort(k, kind="stable")
+        xs = xf[order]
+        ne = cnt > 0
+        starts = np.concatenate([[0], np.cumsum(cnt)[:-1]]).astype(np.int64)[ne]
+        lo[ne] = np.minimum.reduceat(xs, starts, axis=0)
+        hi[ne] = np.maximum.reduceat(xs, starts, axis=0)
+        return cnt, lo, hi
+
+    cnt, lo, hi = boxes(key, nleaf)
+    ocnt, olo, ohi = boxes(okey, 8 * nleaf)
     cnt = cnt.reshape(ns, ns, ns)
     lo = lo.reshape(ns, ns, ns, 3)
     hi = hi.reshape(ns, ns, ns, 3)
+    ocnt = ocnt.reshape(ns, ns, ns, 8)
+    olo = olo.reshape(ns, ns, ns, 8, 3)
+    ohi = ohi.reshape(ns, ns, ns, 8, 3)
     g = np.arange(ns)
     C = np.meshgrid(g, g, g, indexing="ij")
     d2_sing = 42.25 * sigma * sigma
@@ -150,14 +161,14 @@ def p2p_work(x, L, depth, R, sigma):
         nb = [C[d] + t[d] for d in range(3)]
         sh = [np.floor_divide(nb[d], ns) * L for d in range(3)]
         ix = [np.mod(nb[d], ns) for d in range(3)]
-        cn = cnt[ix[0], ix[1], ix[2]]
-        d2 = np.zeros_like(cnt)
+        cn = ocnt[ix[0], ix[1], ix[2]]                      # (ns,ns,ns,8)
+        d2 = np.zeros_like(cn)
         for d in range(3):
-            slo = lo[ix[0], ix[1], ix[2], d] + sh[d]
-            shi = hi[ix[0], ix[1], ix[2], d] + sh[d]
-            gap = np.maximum(0.0, np.maximum(slo - hi[..., d], lo[..., d] - shi))
+            slo = olo[ix[0], ix[1], ix[2], :, d] + sh[d][..., None]
+            shi = ohi[ix[0], ix[1], ix[2], :, d] + sh[d][..., None]
+            gap = np.maximum(0.0, np.maximum(slo - hi[..., d][..., None], lo[..., d][..., None] - shi))
             d2 += gap * gap
-        pairs = cnt * cn
+        pairs = cnt[..., None] * cn
         sing = d2 >= d2_sing
         p_g += float(pairs[sing].sum())
         p_s += float(pairs[~sing].sum())

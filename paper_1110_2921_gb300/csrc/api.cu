@@ -376,6 +376,8 @@ int build_impl(Ctx *c, int64_t n, const void *x)
     if ((st = ensure(c, c->scan_part, (size_t)((c->nleaf + 1023) / 1024 + 1) * sizeof(int), "scan"))) return st;
     if ((st = ensure(c, c->maxleaf, sizeof(int), "max leaf"))) return st;
     if ((st = ensure(c, c->bbox, (size_t)c->nleaf * 2 * sizeof(float4), "leaf boxes"))) return st;
+    if ((st = ensure(c, c->oct_start, (size_t)c->nleaf * 8 * sizeof(int), "octant starts"))) return st;
+    if ((st = ensure(c, c->oct_box, (size_t)c->nleaf * 16 * sizeof(float4), "octant boxes"))) return st;
     if (c->cfg.method == VFMM_METHOD_FMM) {
         c->lvl_off.assign(D + 2, 0);
         size_t tot = 0;
@@ -494,7 +496,7 @@ int vfmm_destroy(vfmm_handle h)
     Ctx *c = &h->c;
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->xs, &c->gs, &c->perm, &c->keys, &c->leaf_start, &c->counts, &c->fill, &c->tmpidx,
-                      &c->scan_part, &c->err, &c->maxleaf, &c->bbox, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->ufar,
+                      &c->scan_part, &c->err, &c->maxleaf, &c->bbox, &c->oct_start, &c->oct_box, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->ufar,
                       &c->sfar, &c->gfar, &c->adj_u, &c->adj_g1, &c->adj_g2, &c->rk_u1, &c->rk_s1, &c->rk_u2, &c->rk_s2, &c->rk_x1, &c->rk_g1, &c->diag, &c->rg_om, &c->rg_r, &c->rg_d, &c->rg_q, &c->rg_t1, &c->rg_t2, &c->rg_dots, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->m2m_f64,
                       &c->lattice_f64, &c->root_m, &c->kblocks, &c->hx, &c->hg, &c->hu, &c->hs};
     for (DevBuf *b : bufs) release(*b);

@@ -189,11 +189,11 @@ constexpr int P3_TILE = 64;      // staged sources
 
 template <int MODE>
 __device__ __forceinline__ void tile3(const P3Const &k, const float (&xi)[P3_TPT][3], const float (&gi)[P3_TPT][3],
-                                      const float4 *sx, const float4 *sg, const float4 *sc, int cnt,
+                                      const float4 *sx, const float4 *sg, const float4 *sc, int j0, int j1,
                                       Acc3 (&acc)[P3_TPT])
 {
 #pragma unroll 2
-    for (int j = 0; j < cnt; ++j) {
+    for (int j = j0; j < j1; ++j) {
         float4 xj = sx[j], gj = sg[j], cj = sc[j];
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) pair3<MODE>(k, xi[q][0], xi[q][1], xi[q][2], gi[q][0], gi[q][1], gi[q][2], xj, gj, cj, acc[q]);
@@ -270,13 +270,15 @@ constexpr double INV_4PI_D = 0.0795774715459476679;
 
 __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict__ xs, const float4 *__restrict__ gs,
                                                         const int *__restrict__ ls, const float4 *__restrict__ bbox,
-                                                        int nside, int log2n, int R, int direct_K, float leaf_w,
-                                                        P3Const kc,
+                                                        const int *__restrict__ oct_start,
+                                                        const float4 *__restrict__ oct_box, int nside, int log2n,
+                                                        int R, int direct_K, float leaf_w, P3Const kc,
                                                         const float *__restrict__ ufar, const float *__restrict__ sfar,
                                                         const int *__restrict__ perm, float *__restrict__ u_out,
                                                         float *__restrict__ s_out)
 {
     __shared__ float4 sx[P3_TILE], sg[P3_TILE], sc[P3_TILE];
+    __shared__ int ost[9];
     const int leaf = blockIdx.x;
     const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
     const int tb = ls[leaf], te = ls[leaf + 1];
@@ -317,16 +319,25 @@ __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict
                     int nx = cx + ox, ny = cy + oy, nz = cz + oz;
                     int sl = ((nx & (nside - 1)) * nside + (ny & (nside - 1))) * nside + (nz & (nside - 1));
                     float shx = kc.L * (float)(nx >> log2n), shy = kc.L * (float)(ny >> log2n), shz = kc.L * (float)(nz >> log2n);
-                    // closest approach of the two leaf boxes selects the inner loop (block-uniform)
-                    float4 slo = bbox[2 * sl], shi = bbox[2 * sl + 1];
-                    float gx = fmaxf(0.f, fmaxf(slo.x + shx - thi.x, tlo.x - shi.x - shx));
-                    float gy = fmaxf(0.f, fmaxf(slo.y + shy - thi.y, tlo.y - shi.y - shy));
-                    float gz = fmaxf(0.f, fmaxf(slo.z + shz - thi.z, tlo.z - shi.z - shz));
-                    float d2 = gx * gx + gy * gy + gz * gz;
-                    const int mode = d2 >= kc.d2_singular ? 2 : (d2 >= kc.d2_series ? 1 : 0);
+                    // closest approach of the target leaf box and each source octant box selects
+                    // the inner loop for that octant (warp-uniform)
+                    int modes = 0;
+#pragma unroll
+                    for (int o = 0; o < 8; ++o) {
+                        float4 slo = oct_box[16 * sl + 2 * o], shi = oct_box[16 * sl + 2 * o + 1];
+                        float gx = fmaxf(0.f, fmaxf(slo.x + shx - thi.x, tlo.x - shi.x - shx));
+                        float gy = fmaxf(0.f, fmaxf(slo.y + shy - thi.y, tlo.y - shi.y - shy));
+                        float gz = fmaxf(0.f, fmaxf(slo.z + shz - thi.z, tlo.z - shi.z - shz));
+                        float d2 = gx * gx + gy * gy + gz * gz;
+                        int mode = d2 >= kc.d2_singular ? 2 : (d2 >= kc.d2_series ? 1 : 0);
+                        modes |= mode << (2 * o);
+                    }
                     // sources relative to the target leaf centre, with the image shift
                     float ox0 = shx - zx, ox1 = shy - zy, ox2 = shz - zz;
                     int sb = ls[sl], se = ls[sl + 1];
+                    __syncwarp();
+                    if (threadIdx.x < 8) ost[threadIdx.x] = oct_start[8 * sl + threadIdx.x];
+                    if (threadIdx.x == 8) ost[8] = se - sb;
                     for (int s0 = sb; s0 < se; s0 += P3_TILE) {
                         int cnt = min(P3_TILE, se - s0);
                         __syncwarp();
@@ -338,9 +349,21 @@ __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict
                             sc[j] = make_float4(g.y * a2 - g.z * a1, g.z * a0 - g.x * a2, g.x * a1 - g.y * a0, 0.f);
                         }
                         __syncwarp();
-                        if (mode == 2) tile3<2>(kc, xi, gi, sx, sg, sc, cnt, acc);
-                        else if (mode == 1) tile3<1>(kc, xi, gi, sx, sg, sc, cnt, acc);
-                        else tile3<0>(kc, xi, gi, sx, sg, sc, cnt, acc);
+                        const int c0 = s0 - sb, c1 = c0 + cnt;
+                        // runs of consecutive octants with the same inner loop
+                        int o = 0;
+                        while (o < 8) {
+                            const int mode = (modes >> (2 * o)) & 3;
+                            int o2 = o + 1;
+                            while (o2 < 8 && ((modes >> (2 * o2)) & 3) == mode) ++o2;
+                            int j0 = max(ost[o], c0) - c0, j1 = min(ost[o2], c1) - c0;
+                            if (j0 < j1) {
+                                if (mode == 2) tile3<2>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
+                                else if (mode == 1) tile3<1>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
+                                else tile3<0>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
+                            }
+                            o = o2;
+                        }
                     }
                 }
         // u = s^2 (A x x^ - U), S = s^3 (A x gamma + D x x^ - E), times 1/(4 pi)
@@ -474,6 +497,7 @@ int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, 
         dim3 grid3((unsigned)c->nleaf, (unsigned)chunks3);
         k_p2p_f32<<<grid3, P3_THREADS, 0, c->stream>>>((const float4 *)c->xs.p, (const float4 *)c->gs.p,
                                                        (const int *)c->leaf_start.p, (const float4 *)c->bbox.p,
+                                                       (const int *)c->oct_start.p, (const float4 *)c->oct_box.p,
                                                        c->nside, log2n, R, direct_K, (float)c->leaf_w, kc,
                                                        (const float *)ufar, (const float *)sfar, (const int *)c->perm.p,
                                                        (float *)u_out, (float *)s_out);

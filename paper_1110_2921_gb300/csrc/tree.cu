@@ -1,10 +1,10 @@
-// Uniform periodic octree: wrap, leaf key, counting sort, per-leaf index sort, gather.
+// Uniform periodic octree: wrap, leaf key, counting sort, per-leaf sort, gather.
 //
 // The paper builds its tree on the CPU (Section 2.2); here every step runs on the GPU.
 // Keys are row-major leaf indices (ix * n + iy) * n + iz at depth D.  The sort is a counting
 // sort (atomic histogram, three-kernel exclusive scan, atomic scatter) followed by a sort of
-// each leaf's particle indices, which makes the final order deterministic: within a leaf,
-// particles appear in increasing caller index.
+// each leaf's particles by (octant of the leaf, caller index), which makes the final order
+// deterministic and each octant's particles contiguous.
 #include "common.cuh"
 #include "vfmm_internal.h"
 
@@ -118,22 +118,38 @@ __global__ void k_scatter(int64_t n, const int *__restrict__ keys, const int *__
     tmpidx[pos] = (int)i;
 }
 
-// One block per leaf: bitonic sort of the leaf's indices in shared memory, then write the
-// permutation and the wrapped, sorted positions.
+// One block per leaf: sort the leaf's particles by (octant of the leaf, caller index) with a
+// bitonic sort in shared memory, then write the permutation, the wrapped sorted positions,
+// the leaf box, and the start and box of each octant (used to pick the P2P inner loop).
+__device__ __forceinline__ int f2ord(float f) { return __float_as_int(f); }  // positions are >= 0
+
 template <typename TIn, typename T>
 __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict__ tmpidx, const TIn *__restrict__ x,
-                            double L, int *__restrict__ perm, typename V4<T>::type *__restrict__ xs,
-                            float4 *__restrict__ bbox, int *__restrict__ err)
+                            double L, int nside, int *__restrict__ perm, typename V4<T>::type *__restrict__ xs,
+                            float4 *__restrict__ bbox, int *__restrict__ oct_start, float4 *__restrict__ oct_box,
+                            int *__restrict__ err)
 {
-    __shared__ int s[LEAF_SORT_CAP];
-    __shared__ float red[6][8];
+    __shared__ unsigned long long s[LEAF_SORT_CAP];
+    __shared__ int ocnt[8], omin[8][3], omax[8][3];
     int leaf = blockIdx.x;
     int b = start[leaf], e = start[leaf + 1];
     int cnt = e - b;
+    if (threadIdx.x < 8) {
+        ocnt[threadIdx.x] = 0;
+        for (int d = 0; d < 3; ++d) {
+            omin[threadIdx.x][d] = 0x7f7fffff;  // FLT_MAX bits
+            omax[threadIdx.x][d] = 0;
+        }
+    }
     if (cnt <= 0) {
         if (threadIdx.x == 0) {
             bbox[2 * leaf] = make_float4(3e38f, 3e38f, 3e38f, 0.f);
             bbox[2 * leaf + 1] = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
+        }
+        if (threadIdx.x < 8) {
+            oct_start[8 * leaf + threadIdx.x] = 0;
+            oct_box[16 * leaf + 2 * threadIdx.x] = make_float4(3e38f, 3e38f, 3e38f, 0.f);
+            oct_box[16 * leaf + 2 * threadIdx.x + 1] = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
         }
         return;
     }
@@ -141,9 +157,28 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
         if (threadIdx.x == 0) atomicOr(err, ERRBIT_LEAF_OVERFLOW);
         return;
     }
+    const int cz = leaf % nside, cy = (leaf / nside) % nside, cx = leaf / (nside * nside);
+    const double invL = 1.0 / L;
+    const double s2 = 2.0 * nside * invL;
     int m = 1;
     while (m < cnt) m <<= 1;
-    for (int k = threadIdx.x; k < m; k += blockDim.x) s[k] = k < cnt ? tmpidx[b + k] : INT_MAX;
+    __syncthreads();
+    for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        unsigned long long key = ~0ull;
+        if (k < cnt) {
+            int i = tmpidx[b + k];
+            int o = 0;
+            const int cc[3] = {cx, cy, cz};
+            for (int d = 0; d < 3; ++d) {
+                double v = wrap_coord<double>((double)x[3 * (int64_t)i + d], L, invL);
+                int h = (int)(v * s2) - 2 * cc[d];
+                h = h < 0 ? 0 : (h > 1 ? 1 : h);
+                o = 2 * o + h;
+            }
+            key = ((unsigned long long)o << 32) | (unsigned)i;
+        }
+        s[k] = key;
+    }
     __syncthreads();
     for (int size = 2; size <= m; size <<= 1)
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -151,7 +186,7 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
                 int q = k ^ stride;
                 if (q > k) {
                     bool up = (k & size) == 0;
-                    int a = s[k], c = s[q];
+                    unsigned long long a = s[k], c = s[q];
                     if ((a > c) == up) {
                         s[k] = c;
                         s[q] = a;
@@ -160,42 +195,43 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
             }
             __syncthreads();
         }
-    double invL = 1.0 / L;
-    float mn[3] = {3e38f, 3e38f, 3e38f}, mx[3] = {-3e38f, -3e38f, -3e38f};
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-        int i = s[k];
+        unsigned long long key = s[k];
+        int i = (int)(unsigned)(key & 0xffffffffull);
+        int o = (int)(key >> 32);
         perm[b + k] = i;
         T c0 = (T)wrap_coord<double>((double)x[3 * (int64_t)i + 0], L, invL);
         T c1 = (T)wrap_coord<double>((double)x[3 * (int64_t)i + 1], L, invL);
         T c2 = (T)wrap_coord<double>((double)x[3 * (int64_t)i + 2], L, invL);
         xs[b + k] = make_v4<T>(c0, c1, c2, T(0));
+        // boxes of the FP32-rounded positions the P2P kernel sees
         float cf[3] = {(float)c0, (float)c1, (float)c2};
+        atomicAdd(&ocnt[o], 1);
         for (int d = 0; d < 3; ++d) {
-            mn[d] = fminf(mn[d], cf[d]);
-            mx[d] = fmaxf(mx[d], cf[d]);
+            atomicMin(&omin[o][d], f2ord(cf[d]));
+            atomicMax(&omax[o][d], f2ord(cf[d]));
         }
     }
-    // leaf bounding box (of the FP32-rounded positions the P2P kernel sees)
-    for (int d = 0; d < 3; ++d)
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
-            mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
-        }
-    int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0)
-        for (int d = 0; d < 3; ++d) {
-            red[d][w] = mn[d];
-            red[3 + d][w] = mx[d];
-        }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float lo[3], hi[3];
-        for (int d = 0; d < 3; ++d) {
-            lo[d] = red[d][0];
-            hi[d] = red[3 + d][0];
-            for (int q = 1; q < nw; ++q) {
-                lo[d] = fminf(lo[d], red[d][q]);
-                hi[d] = fmaxf(hi[d], red[3 + d][q]);
+        int acc = 0;
+        float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+        for (int o = 0; o < 8; ++o) {
+            oct_start[8 * leaf + o] = acc;
+            acc += ocnt[o];
+            if (ocnt[o] > 0) {
+                float l[3], hh[3];
+                for (int d = 0; d < 3; ++d) {
+                    l[d] = __int_as_float(omin[o][d]);
+                    hh[d] = __int_as_float(omax[o][d]);
+                    lo[d] = fminf(lo[d], l[d]);
+                    hi[d] = fmaxf(hi[d], hh[d]);
+                }
+                oct_box[16 * leaf + 2 * o] = make_float4(l[0], l[1], l[2], 0.f);
+                oct_box[16 * leaf + 2 * o + 1] = make_float4(hh[0], hh[1], hh[2], 0.f);
+            } else {
+                oct_box[16 * leaf + 2 * o] = make_float4(3e38f, 3e38f, 3e38f, 0.f);
+                oct_box[16 * leaf + 2 * o + 1] = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
             }
         }
         bbox[2 * leaf] = make_float4(lo[0], lo[1], lo[2], 0.f);
@@ -219,10 +255,10 @@ template <typename TIn, typename T> static int tree_impl(Ctx *c, const TIn *x)
     k_scan_parts<<<1, 1024, 0, st>>>(nparts, part, start + nleaf);
     k_scan_add<<<(int)((nleaf + 255) / 256), 256, 0, st>>>(nleaf, start, part);
     k_scatter<<<nb, 256, 0, st>>>(n, (int *)c->keys.p, start, (int *)c->fill.p, (int *)c->tmpidx.p);
-    k_leaf_sort<TIn, T><<<(unsigned)nleaf, 256, 0, st>>>(start, (int *)c->tmpidx.p, x, c->cfg.box,
-                                                         (int *)c->perm.p,
-                                                         (typename V4<T>::type *)c->xs.p, (float4 *)c->bbox.p,
-                                                         (int *)c->err.p);
+    k_leaf_sort<TIn, T><<<(unsigned)nleaf, 256, 0, st>>>(start, (int *)c->tmpidx.p, x, c->cfg.box, c->nside,
+                                                         (int *)c->perm.p, (typename V4<T>::type *)c->xs.p,
+                                                         (float4 *)c->bbox.p, (int *)c->oct_start.p,
+                                                         (float4 *)c->oct_box.p, (int *)c->err.p);
     c->launches += 5;  // k_keys, three scan kernels and k_scatter precede k_leaf_sort
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;

@@ -14,7 +14,7 @@ namespace vfmm {
 constexpr int PMAX = 16;          // largest supported expansion order
 constexpr int NPHASE = 8;         // timed phases (see vfmm_get_timings)
 constexpr int MAX_DEPTH = 8;      // deepest octree level
-constexpr int LEAF_SORT_CAP = 4096;  // per-leaf index sort capacity
+constexpr int LEAF_SORT_CAP = 4096;  // per-leaf sort capacity (32 KB of 64-bit keys)
 constexpr int OUT_ROWS = 128;     // rows of every packed translation matrix (output coefficients, padded)
 constexpr int NT = 343;           // M2L offsets t in [-3,3]^3
 
@@ -84,6 +84,7 @@ struct Ctx {
     // device buffers
     DevBuf xs, gs, perm, keys, leaf_start, counts, fill, tmpidx, scan_part, err, maxleaf;
     DevBuf bbox;                   // per leaf: float4 lo, float4 hi of its particles
+    DevBuf oct_start, oct_box;     // per leaf: 8 octant starts (relative), 8 x (lo, hi) octant boxes
     DevBuf mexp, lexp;             // all levels, T
     DevBuf mhi, mlo;               // tensor-core copies of the multipoles (largest level)
     DevBuf ufar, sfar, gfar;       // far-field u, S (or grad u) in sorted order, T
