@@ -36,7 +36,7 @@ constexpr int TC_A_BYTES = TC_M * TC_KBYTES;     // 8 KB
 constexpr int TC_B_BYTES = TC_N * TC_KBYTES;     // 12 KB
 constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 40 KB
 constexpr int TC_MAXKB = 256;                                    // k-blocks per parity (<= 189 used)
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 64 + TC_MAXKB * 16 + TC_CELLS * 4;
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 128 + TC_MAXKB * 16 + TC_CELLS * 4;
 constexpr int TC_TMEM_COLS = 256;
 constexpr long long TC_WAIT_LIMIT = 1LL << 26;
 
@@ -83,6 +83,19 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// one-dimensional TMA bulk copy global -> shared (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 template <bool BF16>
 __device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
 {
@@ -104,16 +117,32 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Warp-specialised pipeline: warp 0 lane 0 issues the MMAs; warps 1..4 (128 producer threads)
+// gather the multipole rows with cp.async and release a stage (fence.proxy.async + arrive on
+// full[s]) TC_PF stages after issuing it; producer thread 0 also moves the two pre-tiled
+// translation-matrix tiles with TMA bulk copies (expect_tx on full[s]).  tcgen05.commit on
+// empty[s] returns the slot to the producers.  No CTA-wide barrier inside the main loop.
+// Producer release lag.  A stage is released after the producer has issued TC_PF later stages,
+// and issuing stage i waits for the MMAs of stage i - TC_STAGES; TC_STAGES - TC_PF >= 3 keeps an
+// MMA queued behind the running one (a lag of 4 of 5 stages serialised the MMAs).
+constexpr int TC_PF = 2;
+constexpr int TC_WS_THREADS = 32 + TC_THREADS;  // MMA warp + 4 producer warps
+
 template <bool BF16>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcParams tp)
+__global__ void __launch_bounds__(TC_WS_THREADS, 1) k_m2l_tc(TcParams tp)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-align the stage area
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *stages = base;
-    uint64_t *bars = (uint64_t *)(base + TC_STAGES * TC_STAGE_BYTES);
-    uint32_t *tmem_slot = (uint32_t *)(bars + TC_STAGES);
-    int4 *kb_s = (int4 *)(base + TC_STAGES * TC_STAGE_BYTES + 64);
+    uint64_t *full = (uint64_t *)(base + TC_STAGES * TC_STAGE_BYTES);
+    uint64_t *empty = full + TC_STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(empty + TC_STAGES);
+    int4 *kb_s = (int4 *)(base + TC_STAGES * TC_STAGE_BYTES + 128);
     int *cell_s = (int *)(kb_s + TC_MAXKB);
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -121,9 +150,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcParams tp)
     const int n = tp.n, half = n >> 1;
     const int64_t cell0 = (int64_t)blockIdx.x * TC_CELLS;
     const int nkb = min(tp.kb_cnt[g], TC_MAXKB);
-    const int4 *kbl = kb_s;
-    for (int q = tid; q < nkb; q += TC_THREADS) kb_s[q] = tp.kb[tp.kb_off[g] + q];
-    for (int q = tid; q < TC_CELLS; q += TC_THREADS) {
+    for (int q = tid; q < nkb; q += TC_WS_THREADS) kb_s[q] = tp.kb[tp.kb_off[g] + q];
+    for (int q = tid; q < TC_CELLS; q += TC_WS_THREADS) {
         int64_t P = cell0 + q;
         int px = (int)(P / ((int64_t)half * half)), py = (int)((P / half) % half), pz = (int)(P % half);
         int cx = 2 * px + ((g >> 2) & 1), cy = 2 * py + ((g >> 1) & 1), cz = 2 * pz + (g & 1);
@@ -135,7 +163,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcParams tp)
     const int esz = BF16 ? 2 : 4;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), TC_THREADS + 1);  // 128 producer arrivals + 1 expect_tx arrival
+            mbar_init(smem_u32(&empty[s]), 1);              // tcgen05.commit
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
@@ -148,107 +179,104 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcParams tp)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
-
-    // per-thread B slots: chunk v = tid + 128 j, row nrow = 8 (v >> 5) + (v & 7), k-group (v >> 3) & 3
-    int slot_cx[6], slot_cy[6], slot_cz[6], slot_comp[6], slot_kg[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        int v = tid + TC_THREADS * j;
-        int nrow = 8 * (v >> 5) + (v & 7);
-        slot_kg[j] = (v >> 3) & 3;
-        int q = nrow / 3;
-        slot_comp[j] = nrow - 3 * q;
-        int64_t P = cell0 + q;
-        int px = (int)(P / ((int64_t)half * half)), py = (int)((P / half) % half), pz = (int)(P % half);
-        slot_cx[j] = 2 * px + ((g >> 2) & 1);
-        slot_cy[j] = 2 * py + ((g >> 1) & 1);
-        slot_cz[j] = 2 * pz + (g & 1);
-    }
-    const unsigned char *Ahi = (const unsigned char *)tp.Ahi, *Alo = (const unsigned char *)tp.Alo;
-    const unsigned char *Bhi = (const unsigned char *)tp.Bhi, *Blo = (const unsigned char *)tp.Blo;
-    const size_t row_bytes = (size_t)pc * esz;
-
-    auto load_stage = [&](int i) {
-        int kbi = i / nchunk, ch = i - kbi * nchunk;
-        int4 kb = kbl[kbi];
-        unsigned char *st = stages + (i % TC_STAGES) * TC_STAGE_BYTES;
-        uint32_t sA = smem_u32(st), sAl = sA + TC_A_BYTES, sB = sAl + TC_A_BYTES, sBl = sB + TC_B_BYTES;
-        const unsigned char *ah = Ahi + ((size_t)kb.x * nchunk + ch) * TC_A_BYTES;
-        const unsigned char *al = Alo + ((size_t)kb.x * nchunk + ch) * TC_A_BYTES;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int v = tid + TC_THREADS * j;  // 512 chunks of 16 B
-            cp_async16(sA + 16 * v, ah + 16 * v);
-            cp_async16(sAl + 16 * v, al + 16 * v);
-        }
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            int v = tid + TC_THREADS * j;
-            int sx = (slot_cx[j] + kb.y) & (n - 1);
-            int sy = (slot_cy[j] + kb.z) & (n - 1);
-            int sz = (slot_cz[j] + kb.w) & (n - 1);
-            int64_t src = ((int64_t)sx * n + sy) * n + sz;
-            size_t off = (size_t)(src * 3 + slot_comp[j]) * row_bytes + (size_t)ch * TC_KBYTES + 16 * slot_kg[j];
-            cp_async16(sB + 16 * v, Bhi + off);
-            cp_async16(sBl + 16 * v, Blo + off);
-        }
-    };
-
-    // instruction descriptor: D f32, A/B bf16 (1) or tf32 (2), K-major, N = 192, M = 128
-    const uint32_t fmt = BF16 ? 1u : 2u;
-    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-                           ((uint32_t)(TC_M >> 4) << 24);
     bool ok = true;
 
-    // prologue
-#pragma unroll
-    for (int i = 0; i < TC_PREFETCH; ++i) {
-        if (i < nk) load_stage(i);
-        cp_async_commit();
-    }
-    for (int i = 0; i < nk; ++i) {
-        const int s = i % TC_STAGES;
-        const int ip = i + TC_PREFETCH;
-        // the slot of stage ip was last read by the MMAs of iteration ip - TC_STAGES = i - 2
-        if (ip < nk && ip >= TC_STAGES) {
-            int pi = ip - TC_STAGES;
-            ok = mbar_wait(smem_u32(&bars[pi % TC_STAGES]), (uint32_t)((pi / TC_STAGES) & 1));
-        }
-        if (ip < nk && ok) load_stage(ip);
-        cp_async_commit();
-        cp_async_wait<TC_PREFETCH>();
-        fence_proxy_async();
-        // one barrier: stage i is complete in every thread, and every bounded wait succeeded
-        if (!__syncthreads_and(ok ? 1 : 0)) {
-            ok = false;
-            break;
-        }
+    if (warp == 0) {
+        // ------------------------------- MMA issuer -------------------------------
         if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            unsigned char *st = stages + s * TC_STAGE_BYTES;
-            uint32_t sA = smem_u32(st), sAl = sA + TC_A_BYTES, sB = sAl + TC_A_BYTES, sBl = sB + TC_B_BYTES;
+            const uint32_t fmt = BF16 ? 1u : 2u;
+            const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                                   ((uint32_t)(TC_M >> 4) << 24);
+            for (int i = 0; i < nk; ++i) {
+                const int s = i % TC_STAGES;
+                if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((i / TC_STAGES) & 1))) {
+                    ok = false;
+                    break;
+                }
+                fence_proxy_async();  // producer cp.async writes (generic proxy) before the MMA reads
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                unsigned char *st = stages + s * TC_STAGE_BYTES;
+                uint32_t sA = smem_u32(st), sAl = sA + TC_A_BYTES, sB = sAl + TC_A_BYTES, sBl = sB + TC_B_BYTES;
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                uint32_t koff = 256u * ks;  // two 16-byte k-groups per MMA
-                uint64_t dAh = make_desc(sA + koff, 128, 512), dAl = make_desc(sAl + koff, 128, 512);
-                uint64_t dBh = make_desc(sB + koff, 128, 512), dBl = make_desc(sBl + koff, 128, 512);
-                uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
-                mma_issue<BF16>(tmem, dAh, dBh, idesc, acc0);
-                mma_issue<BF16>(tmem, dAh, dBl, idesc, 1u);
-                mma_issue<BF16>(tmem, dAl, dBh, idesc, 1u);
+                for (int ks = 0; ks < 2; ++ks) {
+                    uint32_t koff = 256u * ks;
+                    uint64_t dAh = make_desc(sA + koff, 128, 512), dAl = make_desc(sAl + koff, 128, 512);
+                    uint64_t dBh = make_desc(sB + koff, 128, 512), dBl = make_desc(sBl + koff, 128, 512);
+                    uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
+                    mma_issue<BF16>(tmem, dAh, dBh, idesc, acc0);
+                    mma_issue<BF16>(tmem, dAh, dBl, idesc, 1u);
+                    mma_issue<BF16>(tmem, dAl, dBh, idesc, 1u);
+                }
+                mma_commit(smem_u32(&empty[s]));
             }
-            mma_commit(smem_u32(&bars[s]));
         }
+    } else {
+        // ------------------------------- producers ---------------------------------
+        const int ptid = tid - 32;
+        int slot_cx[6], slot_cy[6], slot_cz[6], slot_comp[6], slot_kg[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            int v = ptid + TC_THREADS * j;
+            int nrow = 8 * (v >> 5) + (v & 7);
+            slot_kg[j] = (v >> 3) & 3;
+            int q = nrow / 3;
+            slot_comp[j] = nrow - 3 * q;
+            int cell = cell_s[q];
+            slot_cz[j] = cell % n;
+            slot_cy[j] = (cell / n) % n;
+            slot_cx[j] = cell / (n * n);
+        }
+        const unsigned char *Ahi = (const unsigned char *)tp.Ahi, *Alo = (const unsigned char *)tp.Alo;
+        const unsigned char *Bhi = (const unsigned char *)tp.Bhi, *Blo = (const unsigned char *)tp.Blo;
+        const size_t row_bytes = (size_t)pc * esz;
+        for (int i = 0; i < nk + TC_PF; ++i) {
+            if (i < nk) {
+                const int s = i % TC_STAGES;
+                if (i >= TC_STAGES &&
+                    !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((i / TC_STAGES) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                int kbi = i / nchunk, ch = i - kbi * nchunk;
+                int4 kb = kb_s[kbi];
+                unsigned char *st = stages + s * TC_STAGE_BYTES;
+                uint32_t sA = smem_u32(st), sAl = sA + TC_A_BYTES, sB = sAl + TC_A_BYTES, sBl = sB + TC_B_BYTES;
+                if (ptid == 0) {
+                    uint32_t fb = smem_u32(&full[s]);
+                    mbar_expect_tx(fb, 2 * TC_A_BYTES);
+                    bulk_g2s(sA, Ahi + ((size_t)kb.x * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
+                    bulk_g2s(sAl, Alo + ((size_t)kb.x * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
+                }
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    int v = ptid + TC_THREADS * j;
+                    int sx = (slot_cx[j] + kb.y) & (n - 1);
+                    int sy = (slot_cy[j] + kb.z) & (n - 1);
+                    int sz = (slot_cz[j] + kb.w) & (n - 1);
+                    int64_t src = ((int64_t)sx * n + sy) * n + sz;
+                    size_t off = (size_t)(src * 3 + slot_comp[j]) * row_bytes + (size_t)ch * TC_KBYTES + 16 * slot_kg[j];
+                    cp_async16(sB + 16 * v, Bhi + off);
+                    cp_async16(sBl + 16 * v, Blo + off);
+                }
+            }
+            cp_async_commit();
+            if (i >= TC_PF) {
+                // this thread's copies of stage i - TC_PF have landed: publish them
+                cp_async_wait<TC_PF>();
+                fence_proxy_async();
+                mbar_arrive(smem_u32(&full[(i - TC_PF) % TC_STAGES]));
+            }
+        }
+        cp_async_wait<0>();
     }
-    // all threads agree on ok (a failed wait is seen by every thread on the same barrier)
-    if (ok && nk > 0) {
+    // epilogue: wait for the last MMAs (bounded), then warps 0..3 read TMEM lanes 32w..32w+31
+    if (ok && nk > 0 && warp < 4) {
         int li = nk - 1;
-        ok = mbar_wait(smem_u32(&bars[li % TC_STAGES]), (uint32_t)((li / TC_STAGES) & 1));
+        ok = mbar_wait(smem_u32(&empty[li % TC_STAGES]), (uint32_t)((li / TC_STAGES) & 1));
     }
     ok = __syncthreads_and(ok ? 1 : 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (ok) {
-        // epilogue: warp w owns TMEM lanes 32w..32w+31 = output coefficients
+    if (ok && warp < 4) {
         const int k = 32 * warp + (tid & 31);
         float *C = tp.C;
 #pragma unroll 1
@@ -269,9 +297,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_m2l_tc(TcParams tp)
                 C[((int64_t)cell_s[q] * 3 + comp) * pc + k] = __uint_as_float(r[e]);
             }
         }
-    } else {
-        if (tid == 0) atomicOr(tp.err, ERRBIT_TIMEOUT);
-        cp_async_wait<0>();  // this thread's copies in flight
+    } else if (!ok && tid == 0) {
+        atomicOr(tp.err, ERRBIT_TIMEOUT);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -357,9 +384,9 @@ int launch_tc_m2l(Ctx *c, int level, const int4 *kb_dev, const int *kb_off, cons
     tp.err = (int *)c->err.p;
     dim3 grid((unsigned)(ncg / TC_CELLS), 8);
     if (bf16)
-        k_m2l_tc<true><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(tp);
+        k_m2l_tc<true><<<grid, TC_WS_THREADS, TC_SMEM, c->stream>>>(tp);
     else
-        k_m2l_tc<false><<<grid, TC_THREADS, TC_SMEM, c->stream>>>(tp);
+        k_m2l_tc<false><<<grid, TC_WS_THREADS, TC_SMEM, c->stream>>>(tp);
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
 }
