@@ -82,13 +82,14 @@ int launch_gather_gamma(Ctx *c, const void *gamma)
 
 // ---------------------------------------------------------------------------------------
 // P2M (Eq. fmm3dm): Mh_n^m = s_nm sum_j gamma_j Y_n^m((x_j - z)/w) for each leaf.
-// One block per leaf: each thread evaluates the solid harmonics of one particle into shared
-// memory, then each thread owns two coefficients of all three components and sums over the
-// particles (a 3 x 64 by 64 x 128 product per chunk).
+// One block of 128 threads per leaf.  Phase 1: the harmonics of a chunk of particles go to
+// shared memory; each particle's orders m are split over P2M_BS / TP threads (the short
+// diagonal recurrence is repeated by each).  Phase 2: thread j owns coefficient j of all three
+// components and sums gamma_j Y over the chunk (conflict-free rows, broadcast strengths).
 template <typename T> struct P2MCfg {
     static constexpr int TP = sizeof(T) == 4 ? 64 : 32;  // particles per chunk
 };
-constexpr int P2M_BS = 64;
+constexpr int P2M_BS = 128;
 
 template <typename T>
 __global__ void __launch_bounds__(P2M_BS) k_p2m(const typename V4<T>::type *__restrict__ xs,
@@ -97,81 +98,78 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(const typename V4<T>::type *__re
                                                 T *__restrict__ M)
 {
     constexpr int TP = P2MCfg<T>::TP;
+    constexpr int NSPLIT = P2M_BS / TP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *Ysm = (T *)smem_raw;                 // [TP][pc]
-    typename V4<T>::type *gsm = (typename V4<T>::type *)(Ysm + TP * pc);  // [TP]
+    const int ys = pc + 1;                  // padded row stride: the column writes of a warp hit distinct banks
+    T *Ysm = (T *)smem_raw;                                              // [TP][ys]
+    typename V4<T>::type *gsm = (typename V4<T>::type *)(((uintptr_t)(Ysm + TP * ys) + 15) & ~(uintptr_t)15);
     const int leaf = blockIdx.x;
     const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
     const T zx = (cx + T(0.5)) * w, zy = (cy + T(0.5)) * w, zz = (cz + T(0.5)) * w;
     const T invw = T(1) / w;
     const int b = ls[leaf], e = ls[leaf + 1];
     const int nc = (p + 1) * (p + 1);
-    T acc[3][4];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[c][k] = 0;
+    const int q = threadIdx.x % TP, part = threadIdx.x / TP;
+    const int j = threadIdx.x;  // phase-2 coefficient
+    T a0 = 0, a1 = 0, a2 = 0;
     for (int s0 = b; s0 < e; s0 += TP) {
         const int cnt = min(TP, e - s0);
-        for (int t = threadIdx.x; t < TP; t += P2M_BS) {
-            T *row = Ysm + t * pc;
-            if (t < cnt) {
-                typename V4<T>::type xp = xs[s0 + t];
-                gsm[t] = gs[s0 + t];
-                T x = (xp.x - zx) * invw, y = (xp.y - zy) * invw, z = (xp.z - zz) * invw;
-                T r2 = x * x + y * y + z * z;
-                T dre = 1, dim = 0;
-                for (int m = 0; m <= p; ++m) {
-                    if (m > 0) {
-                        T f = -inv2m_t<T>(m);
-                        T nre = f * (x * dre - y * dim);
-                        T nim = f * (x * dim + y * dre);
-                        dre = nre;
-                        dim = nim;
-                    }
-                    T sm = sfac_t<T>(m, m);
-                    row[pk(m, m)] = dre * sm;
-                    if (m > 0) row[pk(m, m) + 1] = dim * sm;
-                    T pre = dre, pim = dim, ppre = 0, ppim = 0;
-                    for (int n = m + 1; n <= p; ++n) {
-                        T c1 = T(2 * n - 1) * z, f = rec_t<T>(n, m);
-                        T cre = (c1 * pre - r2 * ppre) * f;
-                        T cim = (c1 * pim - r2 * ppim) * f;
-                        T sn = sfac_t<T>(n, m);
-                        row[pk(n, m)] = cre * sn;
-                        if (m > 0) row[pk(n, m) + 1] = cim * sn;
-                        ppre = pre;
-                        ppim = pim;
-                        pre = cre;
-                        pim = cim;
-                    }
+        if (q < cnt) {
+            T *row = Ysm + q * ys;
+            typename V4<T>::type xp = xs[s0 + q];
+            if (part == 0) {
+                gsm[q] = gs[s0 + q];
+                for (int jj = nc; jj < pc; ++jj) row[jj] = 0;
+            }
+            T x = (xp.x - zx) * invw, y = (xp.y - zy) * invw, z = (xp.z - zz) * invw;
+            T r2 = x * x + y * y + z * z;
+            T dre = 1, dim = 0;
+            for (int m = 0; m <= p; ++m) {
+                if (m > 0) {
+                    T f = -inv2m_t<T>(m);
+                    T nre = f * (x * dre - y * dim);
+                    T nim = f * (x * dim + y * dre);
+                    dre = nre;
+                    dim = nim;
                 }
-                for (int j = nc; j < pc; ++j) row[j] = 0;
+                if (m % NSPLIT != part) continue;
+                T sm = sfac_t<T>(m, m);
+                row[pk(m, m)] = dre * sm;
+                if (m > 0) row[pk(m, m) + 1] = dim * sm;
+                T pre = dre, pim = dim, ppre = 0, ppim = 0;
+                for (int n = m + 1; n <= p; ++n) {
+                    T c1 = T(2 * n - 1) * z, f = rec_t<T>(n, m);
+                    T cre = (c1 * pre - r2 * ppre) * f;
+                    T cim = (c1 * pim - r2 * ppim) * f;
+                    T sn = sfac_t<T>(n, m);
+                    row[pk(n, m)] = cre * sn;
+                    if (m > 0) row[pk(n, m) + 1] = cim * sn;
+                    ppre = pre;
+                    ppim = pim;
+                    pre = cre;
+                    pim = cim;
+                }
             }
         }
         __syncthreads();
+        if (j < pc) {
 #pragma unroll 8
-        for (int t = 0; t < cnt; ++t) {
-            typename V4<T>::type gv = gsm[t];
-            const T *row = Ysm + t * pc;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (threadIdx.x + k * P2M_BS < pc) {
-                    T yv = row[threadIdx.x + k * P2M_BS];
-                    acc[0][k] += gv.x * yv;
-                    acc[1][k] += gv.y * yv;
-                    acc[2][k] += gv.z * yv;
-                }
+            for (int t = 0; t < cnt; ++t) {
+                typename V4<T>::type gv = gsm[t];
+                T yv = Ysm[t * ys + j];
+                a0 += gv.x * yv;
+                a1 += gv.y * yv;
+                a2 += gv.z * yv;
             }
         }
         __syncthreads();
     }
-    T *out = M + (size_t)leaf * 3 * pc;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (threadIdx.x + k * P2M_BS < pc)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) out[c * pc + threadIdx.x + k * P2M_BS] = acc[c][k];
+    if (j < pc) {
+        T *out = M + (size_t)leaf * 3 * pc;
+        out[j] = a0;
+        out[pc + j] = a1;
+        out[2 * pc + j] = a2;
+    }
 }
 
 int launch_p2m(Ctx *c)
@@ -180,7 +178,11 @@ int launch_p2m(Ctx *c)
     while ((1 << log2n) < c->nside) ++log2n;
     size_t off = c->lvl_off[c->depth];
     const int tp = c->f64 ? P2MCfg<double>::TP : P2MCfg<float>::TP;
-    size_t sm = (size_t)tp * c->pc * c->esz + (size_t)tp * 4 * c->esz;
+    size_t sm = (size_t)tp * (c->pc + 1) * c->esz + 16 + (size_t)tp * 4 * c->esz;
+    if (c->pc > P2M_BS) {
+        c->last_error = "P2M supports at most 128 padded coefficients";
+        return VFMM_ERR_UNSUPPORTED;
+    }
     if (c->f64)
         k_p2m<double><<<(unsigned)c->nleaf, P2M_BS, sm, c->stream>>>(
             (const dvec4 *)c->xs.p, (const dvec4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,
@@ -440,7 +442,7 @@ int launch_root(Ctx *c)
 //   G^z_{a,b} = F_{a+1,b},  G^x_{a,b} = (F_{a+1,b-1} - F_{a+1,b+1})/2,
 //   G^y_{a,b} = i (F_{a+1,b+1} + F_{a+1,b-1})/2.
 // Each particle then evaluates Y_a^b at its offset once and accumulates 27 dot products.
-constexpr int L2P_BS = 128;
+constexpr int L2P_BS = 64;   // one thread per particle of a 64-particle leaf
 
 template <typename T> struct Cx {
     T re, im;
