@@ -28,6 +28,8 @@ template <typename T> __device__ __forceinline__ T inv2m_t(int m);
 template <> __device__ __forceinline__ float inv2m_t<float>(int m) { return c_inv2m_f[m]; }
 template <> __device__ __forceinline__ double inv2m_t<double>(int m) { return c_inv2m_d[m]; }
 
+void set_l2p_tables();
+
 void set_constants(int)
 {
     float sf[(PMAX + 1) * (PMAX + 1)] = {0}, rf[(PMAX + 1) * (PMAX + 1)] = {0}, i2f[PMAX + 1] = {0};
@@ -51,6 +53,7 @@ void set_constants(int)
     cudaMemcpyToSymbol(c_rec_d, rd, sizeof(rd));
     cudaMemcpyToSymbol(c_inv2m_f, i2f, sizeof(i2f));
     cudaMemcpyToSymbol(c_inv2m_d, i2d, sizeof(i2d));
+    set_l2p_tables();
 }
 
 __device__ __forceinline__ int pk(int n, int m) { return m == 0 ? n * n : n * n + 2 * m - 1; }
@@ -443,52 +446,65 @@ int launch_root(Ctx *c)
 //   G^y_{a,b} = i (F_{a+1,b+1} + F_{a+1,b-1})/2.
 // Each particle then evaluates Y_a^b at its offset once and accumulates 27 dot products.
 constexpr int L2P_BS = 64;   // one thread per particle of a 64-particle leaf
+constexpr int NCX_MAX = (PMAX + 1) * (PMAX + 2) / 2;
+__constant__ unsigned char c_cn[NCX_MAX], c_cm[NCX_MAX];  // complex index -> (n, m)
 
-template <typename T> struct Cx {
-    T re, im;
-};
-
-template <typename T> __device__ __forceinline__ Cx<T> getc(const T *P, int n, int m, int nmax)
+void set_l2p_tables()
 {
-    Cx<T> z = {0, 0};
+    unsigned char cn[NCX_MAX], cm[NCX_MAX];
+    int ci = 0;
+    for (int n = 0; n <= PMAX; ++n)
+        for (int m = 0; m <= n; ++m, ++ci) {
+            cn[ci] = (unsigned char)n;
+            cm[ci] = (unsigned char)m;
+        }
+    cudaMemcpyToSymbol(c_cn, cn, sizeof(cn));
+    cudaMemcpyToSymbol(c_cm, cm, sizeof(cm));
+}
+
+template <typename T> struct C2;
+template <> struct C2<float> { typedef float2 type; };
+template <> struct C2<double> { typedef double2 type; };
+
+__device__ __forceinline__ int cix(int n, int m) { return n * (n + 1) / 2 + m; }
+
+// complex coefficient (n, m) of a table in complex layout (m >= 0 stored), any m
+template <typename T>
+__device__ __forceinline__ typename C2<T>::type getcx(const typename C2<T>::type *P, int n, int m, int nmax)
+{
+    typename C2<T>::type z;
+    z.x = 0;
+    z.y = 0;
     if (n < 0 || n > nmax) return z;
     int am = m < 0 ? -m : m;
     if (am > n) return z;
-    if (am == 0) {
-        z.re = P[n * n];
-        return z;
-    }
-    z.re = P[n * n + 2 * am - 1];
-    z.im = P[n * n + 2 * am];
+    z = P[cix(n, am)];
     if (m < 0) {  // (-1)^m conj
-        z.im = -z.im;
+        z.y = -z.y;
         if (am & 1) {
-            z.re = -z.re;
-            z.im = -z.im;
+            z.x = -z.x;
+            z.y = -z.y;
         }
     }
     return z;
 }
 
-// out = D^dir(in) for degrees 0..nmax-1 (in has degrees 0..nmax); dir 0 = x, 1 = y, 2 = z.
-template <typename T> __device__ __forceinline__ void deriv_store(const T *in, int nmax, int dir, int a, int b, T *out)
+// D^dir applied to table `in` (degrees 0..nmax), output entry (a, b), dir 0 = x, 1 = y, 2 = z:
+//   D^z: F_{a+1,b};  D^x: (F_{a+1,b-1} - F_{a+1,b+1})/2;  D^y: i (F_{a+1,b+1} + F_{a+1,b-1})/2
+template <typename T>
+__device__ __forceinline__ typename C2<T>::type dcx(const typename C2<T>::type *in, int nmax, int dir, int a, int b)
 {
-    Cx<T> v;
-    if (dir == 2) {
-        v = getc(in, a + 1, b, nmax);
+    typename C2<T>::type v;
+    if (dir == 2) return getcx<T>(in, a + 1, b, nmax);
+    typename C2<T>::type p1 = getcx<T>(in, a + 1, b + 1, nmax), m1 = getcx<T>(in, a + 1, b - 1, nmax);
+    if (dir == 0) {
+        v.x = T(0.5) * (m1.x - p1.x);
+        v.y = T(0.5) * (m1.y - p1.y);
     } else {
-        Cx<T> p1 = getc(in, a + 1, b + 1, nmax), m1 = getc(in, a + 1, b - 1, nmax);
-        if (dir == 0) {
-            v.re = T(0.5) * (m1.re - p1.re);
-            v.im = T(0.5) * (m1.im - p1.im);
-        } else {
-            // i/2 (p1 + m1)
-            v.re = T(-0.5) * (p1.im + m1.im);
-            v.im = T(0.5) * (p1.re + m1.re);
-        }
+        v.x = T(-0.5) * (p1.y + m1.y);
+        v.y = T(0.5) * (p1.x + m1.x);
     }
-    out[pk(a, b)] = v.re;
-    if (b > 0) out[pk(a, b) + 1] = v.im;
+    return v;
 }
 
 template <typename T>
@@ -498,46 +514,40 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
                                                 const T *__restrict__ Lc, T *__restrict__ ufar, T *__restrict__ sfar,
                                                 T *__restrict__ gfar)
 {
+    typedef typename C2<T>::type T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *F = (T *)smem_raw;            // [3][pc]
-    T *G = F + 3 * pc;               // [3 dir][3 comp][pc]
-    T *H = G + 9 * pc;               // [6 pair][3 comp][pc]
+    const int ncx = (p + 1) * (p + 2) / 2;
+    T2 *F = (T2 *)smem_raw;    // [3][ncx]       local coefficients times s_nm
+    T2 *G = F + 3 * ncx;       // [3 dir][3 comp][ncx]   d_dir psi_comp (degrees < p)
+    T2 *H = G + 9 * ncx;       // [6 pair][3 comp][ncx]  d_a d_b psi_comp (degrees < p - 1)
     const int leaf = blockIdx.x;
     const int b0 = ls[leaf], e0 = ls[leaf + 1];
     if (e0 <= b0) return;
     const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
-    const int nc = (p + 1) * (p + 1);
-    for (int o = threadIdx.x; o < 3 * pc; o += blockDim.x) {
-        int comp = o / pc, j = o - comp * pc;
-        T v = 0;
-        if (j < nc) {
-            int n = 0;
-            while ((n + 1) * (n + 1) <= j) ++n;
-            int r = j - n * n, m = (r + 1) >> 1;
-            v = Lc[(size_t)leaf * 3 * pc + o] * sfac_t<T>(n, m);
-        }
+    for (int o = threadIdx.x; o < 3 * ncx; o += blockDim.x) {
+        int comp = o / ncx, ci = o - comp * ncx;
+        int n = c_cn[ci], m = c_cm[ci];
+        const T *src = Lc + (size_t)leaf * 3 * pc + comp * pc;
+        T sf = sfac_t<T>(n, m);
+        T2 v;
+        v.x = src[pk(n, m)] * sf;
+        v.y = m > 0 ? src[pk(n, m) + 1] * sf : T(0);
         F[o] = v;
     }
     __syncthreads();
-    const int npair1 = p * (p + 1) / 2;  // (a, b) with a < p
-    for (int it = threadIdx.x; it < 9 * npair1; it += blockDim.x) {
-        int q = it % npair1, rest = it / npair1;
+    const int ng = p * (p + 1) / 2;  // entries of degree < p
+    for (int it = threadIdx.x; it < 9 * ng; it += blockDim.x) {
+        int ci = it % ng, rest = it / ng;
         int comp = rest % 3, dir = rest / 3;
-        int a = 0;
-        while ((a + 1) * (a + 2) / 2 <= q) ++a;
-        int bb = q - a * (a + 1) / 2;
-        deriv_store<T>(F + comp * pc, p, dir, a, bb, G + (dir * 3 + comp) * pc);
+        G[(dir * 3 + comp) * ncx + ci] = dcx<T>(F + comp * ncx, p, dir, c_cn[ci], c_cm[ci]);
     }
     __syncthreads();
-    const int npair2 = (p - 1) * p / 2;  // (a, b) with a < p - 1
+    const int nh = (p - 1) * p / 2;  // entries of degree < p - 1
     const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
-    for (int it = threadIdx.x; it < 18 * npair2; it += blockDim.x) {
-        int q = it % npair2, rest = it / npair2;
+    for (int it = threadIdx.x; it < 18 * nh; it += blockDim.x) {
+        int ci = it % nh, rest = it / nh;
         int comp = rest % 3, pr = rest / 3;
-        int a = 0;
-        while ((a + 1) * (a + 2) / 2 <= q) ++a;
-        int bb = q - a * (a + 1) / 2;
-        deriv_store<T>(G + (pa[pr] * 3 + comp) * pc, p - 1, pb[pr], a, bb, H + (pr * 3 + comp) * pc);
+        H[(pr * 3 + comp) * ncx + ci] = dcx<T>(G + (pa[pr] * 3 + comp) * ncx, p - 1, pb[pr], c_cn[ci], c_cm[ci]);
     }
     __syncthreads();
     const T zx = (cx + T(0.5)) * w, zy = (cy + T(0.5)) * w, zz = (cz + T(0.5)) * w;
@@ -546,15 +556,9 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
         typename V4<T>::type xp = xs[i];
         T x = (xp.x - zx) * invw, y = (xp.y - zy) * invw, z = (xp.z - zz) * invw;
         T r2 = x * x + y * y + z * z;
-        T gr[3][3], hs[3][6];
+        T A[27];
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) gr[a][k] = 0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int k = 0; k < 6; ++k) hs[a][k] = 0;
+        for (int v = 0; v < 27; ++v) A[v] = 0;
         T dre = 1, dim = 0;
         for (int m = 0; m < p; ++m) {
             if (m > 0) {
@@ -565,6 +569,8 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
                 dim = nim;
             }
             T pre = dre, pim = dim, ppre = 0, ppim = 0;
+            const T wgt = m > 0 ? T(2) : T(1);  // the pair +-m of sum conj(Y) T
+            int ci = cix(m, m);
             for (int n = m; n < p; ++n) {
                 T cre, cim;
                 if (n == m) {
@@ -579,67 +585,55 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
                     pre = cre;
                     pim = cim;
                 }
-                // sum_b conj(Y) G over b = +-m: weight 2 for m > 0 (real part of conj(Y) G)
-                T wre = m > 0 ? T(2) * cre : cre, wim = m > 0 ? T(2) * cim : T(0);
-                int j = pk(n, m);
+                T wre = wgt * cre, wim = wgt * cim;
 #pragma unroll
-                for (int d = 0; d < 3; ++d)
-#pragma unroll
-                    for (int comp = 0; comp < 3; ++comp) {
-                        const T *Gv = G + (d * 3 + comp) * pc + j;
-                        T acc = wre * Gv[0];
-                        if (m > 0) acc += wim * Gv[1];
-                        gr[comp][d] += acc;
-                    }
+                for (int v = 0; v < 9; ++v) {
+                    T2 t = G[v * ncx + ci];
+                    A[v] += wre * t.x + wim * t.y;
+                }
                 if (n < p - 1) {
 #pragma unroll
-                    for (int pr = 0; pr < 6; ++pr)
-#pragma unroll
-                        for (int comp = 0; comp < 3; ++comp) {
-                            const T *Hv = H + (pr * 3 + comp) * pc + j;
-                            T acc = wre * Hv[0];
-                            if (m > 0) acc += wim * Hv[1];
-                            hs[comp][pr] += acc;
-                        }
+                    for (int v = 0; v < 18; ++v) {
+                        T2 t = H[v * ncx + ci];
+                        A[9 + v] += wre * t.x + wim * t.y;
+                    }
                 }
+                ci += n + 1;
             }
         }
         // psi_c = (1/4pi)(1/w) sum conj(Y) s F; d/dx = (1/w) d/dy
         const T s1 = T(0.0795774715459476679) * invw * invw;
         const T s2 = s1 * invw;
-        // gr[c][a] = d_a psi_c ; hs[c][pair] = d_a d_b psi_c with pairs xx xy xz yy yz zz
-        T u0 = s1 * (gr[2][1] - gr[1][2]);
-        T u1 = s1 * (gr[0][2] - gr[2][0]);
-        T u2 = s1 * (gr[1][0] - gr[0][1]);
-        typename V4<T>::type gp = gs[i];
-        T gk[3] = {gp.x, gp.y, gp.z};
-        // H(c, k, b) = d_k d_b psi_c
-        auto Hc = [&](int comp, int k, int b) -> T {
-            int lo = k < b ? k : b, hi = k < b ? b : k;
+        // A[dir*3 + comp] = d_dir psi_comp ; A[9 + pair*3 + comp] with pairs xx xy xz yy yz zz
+        auto gr = [&](int comp, int dir) -> T { return A[dir * 3 + comp]; };
+        auto Hc = [&](int comp, int kk, int bb) -> T {
+            int lo = kk < bb ? kk : bb, hi = kk < bb ? bb : kk;
             int idx = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
-            return hs[comp][idx];
+            return A[9 + idx * 3 + comp];
         };
-        T S0 = 0, S1 = 0, S2 = 0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            S0 += gk[k] * (Hc(2, k, 1) - Hc(1, k, 2));
-            S1 += gk[k] * (Hc(0, k, 2) - Hc(2, k, 0));
-            S2 += gk[k] * (Hc(1, k, 0) - Hc(0, k, 1));
-        }
-        ufar[3 * (int64_t)i + 0] = u0;
-        ufar[3 * (int64_t)i + 1] = u1;
-        ufar[3 * (int64_t)i + 2] = u2;
+        ufar[3 * (int64_t)i + 0] = s1 * (gr(2, 1) - gr(1, 2));
+        ufar[3 * (int64_t)i + 1] = s1 * (gr(0, 2) - gr(2, 0));
+        ufar[3 * (int64_t)i + 2] = s1 * (gr(1, 0) - gr(0, 1));
         if (sfar) {
+            typename V4<T>::type gp = gs[i];
+            T gk[3] = {gp.x, gp.y, gp.z};
+            T S0 = 0, S1 = 0, S2 = 0;
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                S0 += gk[kk] * (Hc(2, kk, 1) - Hc(1, kk, 2));
+                S1 += gk[kk] * (Hc(0, kk, 2) - Hc(2, kk, 0));
+                S2 += gk[kk] * (Hc(1, kk, 0) - Hc(0, kk, 1));
+            }
             sfar[3 * (int64_t)i + 0] = s2 * S0;
             sfar[3 * (int64_t)i + 1] = s2 * S1;
             sfar[3 * (int64_t)i + 2] = s2 * S2;
         }
         if (gfar) {  // velocity gradient du_a/dx_k = eps_abc d_k d_b psi_c
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                gfar[9 * (int64_t)i + 0 + k] = s2 * (Hc(2, k, 1) - Hc(1, k, 2));
-                gfar[9 * (int64_t)i + 3 + k] = s2 * (Hc(0, k, 2) - Hc(2, k, 0));
-                gfar[9 * (int64_t)i + 6 + k] = s2 * (Hc(1, k, 0) - Hc(0, k, 1));
+            for (int kk = 0; kk < 3; ++kk) {
+                gfar[9 * (int64_t)i + 0 + kk] = s2 * (Hc(2, kk, 1) - Hc(1, kk, 2));
+                gfar[9 * (int64_t)i + 3 + kk] = s2 * (Hc(0, kk, 2) - Hc(2, kk, 0));
+                gfar[9 * (int64_t)i + 6 + kk] = s2 * (Hc(1, kk, 0) - Hc(0, kk, 1));
             }
         }
     }
@@ -650,7 +644,8 @@ int launch_l2p(Ctx *c, bool grad)
     int log2n = 0;
     while ((1 << log2n) < c->nside) ++log2n;
     size_t off = c->lvl_off[c->depth];
-    size_t sm = (size_t)(3 + 9 + 18) * c->pc * c->esz;
+    const int ncx = (c->p + 1) * (c->p + 2) / 2;
+    size_t sm = (size_t)(3 + 9 + 18) * ncx * 2 * c->esz;
     if (c->f64)
         k_l2p<double><<<(unsigned)c->nleaf, L2P_BS, sm, c->stream>>>(
             (const dvec4 *)c->xs.p, (const dvec4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,
