@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--check", type=int, default=16, help="sampled targets for the oracle error (0 = off)")
     ap.add_argument("--cpu-targets", type=int, default=0, help="oracle targets for cpu_baseline (0 = one per host core)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--workload", default="eval", choices=["eval", "timestep"],
+                    help="eval: u + S per step (the metric); timestep: ten Heun steps + one reinitialisation")
     return ap.parse_args()
 
 
@@ -251,10 +253,59 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_timestep(args):
+    """Ten Heun steps (dt = 0.01, core spreading with nu for Re_lambda = 100) and one
+    reinitialisation onto the 256^3 lattice (20 iterations), mixed precision and plain FP32 M2L."""
+    import numpy as np
+    import torch
+    import workload as wl
+    import paper_1110_2921_gb300 as vf
+    from paper_1110_2921_gb300 import build
+    build.build()
+    n = args.n
+    N = n ** 3
+    f = wl.make_vortex_lattice(n, args.k0, 1)
+    nu = wl.viscosity_for_re_lambda(n, args.k0, 1, 100.0)
+    out = {"metric": "Heun step and reinitialisation time at %d^3" % n, "unit": "ms", "nu": nu, "rho_cut": 5.0,
+           "dt": 0.01, "steps": 10, "reinit_iterations": 20, "runs": {}}
+    for m2l in ("bf16x3", "fp32"):
+        X = torch.tensor(f["x"], dtype=torch.float32, device="cuda")
+        G = torch.tensor(f["alpha"], dtype=torch.float32, device="cuda")
+        # rho_cut = 5 keeps 4h leaves with two near rings up to sigma = 1.6 h (1 - q(5) = 1.5e-5)
+        h = vf.VortexFMM(p=args.p, periodic_levels=args.periodic_levels, m2l=m2l, rho_cut=5.0)
+        d0 = h.diagnostics(X, G)
+        sigma = f["sigma"]
+        sigma = h.rk_step(X, G, sigma, 0.01, nu)  # warm-up step
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            sigma = h.rk_step(X, G, sigma, 0.01, nu)
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / 10
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record()
+        xn, gn, res = h.reinit(X, G, sigma, n, iters=20)
+        r1.record()
+        torch.cuda.synchronize()
+        d1 = h.diagnostics(xn, gn)
+        h.close()
+        out["runs"][m2l] = {"ms_per_heun_step": step_ms, "particles_per_s": N / (step_ms / 1e3),
+                            "ms_reinit": r0.elapsed_time(r1), "reinit_residual": res, "sigma_final": sigma,
+                            "total_vorticity_before": d0["total_vorticity"],
+                            "total_vorticity_after_reinit": d1["total_vorticity"],
+                            "sum_gamma2_before": d0["sum_gamma2"], "sum_gamma2_after_reinit": d1["sum_gamma2"]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "timestep":
+        run_timestep(args)
         return
     import numpy as np
     import torch

@@ -138,8 +138,11 @@ int vfmm_eval_adjoint(vfmm_handle h, const void *gamma, double sigma, const void
  * explicit trapezoid (Heun) rule: (u1, S1) at (x, gamma, sigma); (u2, S2) at
  * (x + dt u1, gamma + dt S1, sqrt(sigma^2 + 2 nu dt)); then x += dt (u1 + u2)/2 wrapped into
  * [0, L), gamma += dt (S1 + S2)/2, sigma^2 += 2 nu dt (core spreading, exact).  x, gamma: device
- * n x 3 (caller order), updated in place; sigma: host, updated.  Builds the tree twice; the
- * handle's tree is stale afterwards (call vfmm_build_tree before the next evaluation).
+ * n x 3 (caller order), updated in place; sigma: host, updated.  Builds the tree twice; with
+ * depth 0 and near_rings 0 in the configuration each build takes the ncrit depth made
+ * shallower where the stage's core needs it (2 w >= rho_cut sigma), so growing cores stay
+ * within the two-ring near field.  The handle's tree is stale afterwards (call
+ * vfmm_build_tree before the next evaluation).
  * Errors: n <= 0, NULL pointers, non-finite dt or nu, nu < 0, sigma <= 0 -> VFMM_ERR_ARG. */
 int vfmm_rk_step(vfmm_handle h, int64_t n, void *x, void *gamma, double *sigma, double dt, double nu);
 

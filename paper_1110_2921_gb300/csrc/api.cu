@@ -341,7 +341,7 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
     return VFMM_OK;
 }
 
-int build_impl(Ctx *c, int64_t n, const void *x)
+int build_impl(Ctx *c, int64_t n, const void *x, double sigma_hint = 0.0)
 {
     if (n <= 0) return fail(c, VFMM_ERR_ARG, "n must be > 0");
     if (n > (int64_t)1 << 30) return fail(c, VFMM_ERR_UNSUPPORTED, "n above 2^30 particles");
@@ -356,6 +356,10 @@ int build_impl(Ctx *c, int64_t n, const void *x)
         D = (int)std::lround(std::log(ratio > 1.0 ? ratio : 1.0) / std::log(8.0));
         if (D < 1) D = 1;
         if (D > MAX_DEPTH) D = MAX_DEPTH;
+        // a known core size (time stepping with core spreading): the shallowest change of
+        // depth that keeps the near field within two rings, 2 w >= rho_cut sigma
+        if (sigma_hint > 0.0 && c->cfg.method == VFMM_METHOD_FMM && c->cfg.near_rings == 0)
+            while (D > 1 && 2.0 * (c->cfg.box / (1 << D)) < c->cfg.rho_cut * sigma_hint) --D;
     }
     c->depth = D;
     c->nside = 1 << D;
@@ -575,12 +579,12 @@ int vfmm_rk_step(vfmm_handle h, int64_t n, void *x, void *gamma, double *sigma, 
         if ((st = ensure(c, *b, bytes, "time-step temporaries"))) return st;
     const double L = c->cfg.box;
     // stage 1 at (x, gamma, sigma)
-    if ((st = build_impl(c, n, x))) return st;
+    if ((st = build_impl(c, n, x, s0))) return st;
     if ((st = eval_impl(c, gamma, s0, c->rk_u1.p, c->rk_s1.p))) return st;
     if ((st = launch_axpy3(c, n, x, c->rk_u1.p, nullptr, dt, L, c->rk_x1.p))) return st;
     if ((st = launch_axpy3(c, n, gamma, c->rk_s1.p, nullptr, dt, 0.0, c->rk_g1.p))) return st;
     // stage 2 at (x + dt u1, gamma + dt S1, sqrt(sigma^2 + 2 nu dt))
-    if ((st = build_impl(c, n, c->rk_x1.p))) return st;
+    if ((st = build_impl(c, n, c->rk_x1.p, s1))) return st;
     if ((st = eval_impl(c, c->rk_g1.p, s1, c->rk_u2.p, c->rk_s2.p))) return st;
     if ((st = launch_axpy3(c, n, x, c->rk_u1.p, c->rk_u2.p, 0.5 * dt, L, x))) return st;
     if ((st = launch_axpy3(c, n, gamma, c->rk_s1.p, c->rk_s2.p, 0.5 * dt, 0.0, gamma))) return st;

@@ -79,3 +79,16 @@ def test_overlap_and_precision_128cubed(ratio):
         eu, es = rel_l2(u[tid], uo), rel_l2(s[tid], so)
         print("sigma/h=%.1f %s depth=%d R=%d: u %.3e S %.3e" % (ratio, m2l, info["depth"], info["near_rings"], eu, es))
         assert eu < 1e-4 and es < 1e-3
+
+
+def test_reduced_cutoff_with_spread_cores_128cubed():
+    # rho_cut = 5 (the time-step setting): cores spread to 1.5 h stay on 4h leaves with R = 2;
+    # the dropped smoothing tail 1 - q(5) = 1.5e-5 keeps the p = 10 accuracy
+    f = wl.make_vortex_lattice(128, 4, 1, sigma_over_h=1.5)
+    tid = wl.target_subset(128 ** 3, 24, seed=3)
+    uo, so = oracle.direct(f["x"], f["alpha"], f["sigma"], K=1, targets=tid)
+    u, s, info = run_fmm(f["x"], f["alpha"], f["sigma"], p=10, rho_cut=5.0, periodic_levels=0, m2l="bf16x3")
+    eu, es = rel_l2(u[tid], uo), rel_l2(s[tid], so)
+    print("rho_cut=5 sigma/h=1.5 depth=%d R=%d: u %.3e S %.3e" % (info["depth"], info["near_rings"], eu, es))
+    assert info["depth"] == 5 and info["near_rings"] == 2
+    assert eu < 1e-4 and es < 1e-3
