@@ -255,7 +255,7 @@ template <typename TIn, typename T> static int tree_impl(Ctx *c, const TIn *x)
     k_scan_parts<<<1, 1024, 0, st>>>(nparts, part, start + nleaf);
     k_scan_add<<<(int)((nleaf + 255) / 256), 256, 0, st>>>(nleaf, start, part);
     k_scatter<<<nb, 256, 0, st>>>(n, (int *)c->keys.p, start, (int *)c->fill.p, (int *)c->tmpidx.p);
-    k_leaf_sort<TIn, T><<<(unsigned)nleaf, 256, 0, st>>>(start, (int *)c->tmpidx.p, x, c->cfg.box, c->nside,
+    k_leaf_sort<TIn, T><<<(unsigned)nleaf, 64, 0, st>>>(start, (int *)c->tmpidx.p, x, c->cfg.box, c->nside,
                                                          (int *)c->perm.p, (typename V4<T>::type *)c->xs.p,
                                                          (float4 *)c->bbox.p, (int *)c->oct_start.p,
                                                          (float4 *)c->oct_box.p, (int *)c->err.p);
