@@ -88,21 +88,22 @@ inline float tf32_value(float f)
     return r;
 }
 
-// Tensor-core operand tiles: for each matrix and each 64-byte K chunk, the 128 x 64 B tile in
-// the canonical no-swizzle K-major layout: byte (k/8)*512 + kgroup*128 + (k%8)*16 + (byte in group).
+// Tensor-core operand tiles: for each matrix and each TC_KBYTES-byte K chunk, the 128-row tile
+// in the canonical no-swizzle K-major layout: byte (k/8)*(TC_KG*128) + kgroup*128 + (k%8)*16 +
+// (byte in group).
 void tile_matrix(const std::vector<double> &A, int nc, int pc, bool bf16, unsigned char *hi, unsigned char *lo)
 {
     const int esz = bf16 ? 2 : 4;
-    const int kc = 64 / esz;
+    const int kc = TC_KBYTES / esz;
     const int nchunk = pc / kc;
     for (int ch = 0; ch < nchunk; ++ch) {
-        unsigned char *th = hi + (size_t)ch * 8192, *tl = lo + (size_t)ch * 8192;
+        unsigned char *th = hi + (size_t)ch * TC_A_TILE, *tl = lo + (size_t)ch * TC_A_TILE;
         for (int k = 0; k < 128; ++k)
             for (int e = 0; e < kc; ++e) {
                 int j = ch * kc + e;
                 double a = (k < nc && j < nc) ? A[(size_t)k * nc + j] : 0.0;
-                size_t byte = (size_t)(k / 8) * 512 + (size_t)((e * esz) / 16) * 128 + (size_t)(k % 8) * 16 +
-                              (size_t)((e * esz) % 16);
+                size_t byte = (size_t)(k / 8) * (TC_KG * 128) + (size_t)((e * esz) / 16) * 128 +
+                              (size_t)(k % 8) * 16 + (size_t)((e * esz) % 16);
                 if (bf16) {
                     uint16_t h = bf16_bits((float)a);
                     uint16_t l = bf16_bits((float)(a - (double)bf16_value(h)));
@@ -136,7 +137,7 @@ template <typename T> int build_operators(Ctx *c)
     std::vector<T> m2l((size_t)NT * pc * OUT_ROWS, T(0));
     const bool tc = c->cfg.m2l_prec == VFMM_M2L_TF32X3 || c->cfg.m2l_prec == VFMM_M2L_BF16X3;
     const bool bf16 = c->cfg.m2l_prec == VFMM_M2L_BF16X3;
-    const size_t tile_bytes = (size_t)pc * (bf16 ? 2 : 4) / 64 * 8192;  // all K chunks of one matrix
+    const size_t tile_bytes = (size_t)pc * (bf16 ? 2 : 4) / TC_KBYTES * TC_A_TILE;  // all K chunks of one matrix
     std::vector<unsigned char> thi, tlo;
     if (tc) {
         thi.assign((size_t)NT * tile_bytes, 0);

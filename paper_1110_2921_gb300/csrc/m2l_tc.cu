@@ -14,8 +14,8 @@
 // Mechanics (sm_103a): 128 threads; one elected thread issues tcgen05.mma (M = 128,
 // N = 192, K = 16 bf16 / 8 tf32 per instruction) from shared-memory descriptors in the
 // canonical no-swizzle K-major layout (8-row x 16-byte core matrices; K-adjacent core
-// matrices 128 B apart, 8-row groups 512 B apart); operands stream through a 4-stage
-// cp.async pipeline; tcgen05.commit arrives on one mbarrier per stage so a stage is refilled
+// matrices 128 B apart, 8-row groups TC_KG x 128 B apart); operands stream through a
+// multi-stage pipeline; tcgen05.commit arrives on one mbarrier per stage so a stage is refilled
 // only after the MMAs that read it completed.  Every mbarrier wait is bounded: on timeout
 // the kernel sets an error bit, waits (bounded) for its own loads, frees TMEM and returns.
 #include "common.cuh"
@@ -29,14 +29,15 @@ constexpr int TC_THREADS = 128;
 constexpr int TC_CELLS = 64;
 constexpr int TC_N = 3 * TC_CELLS;          // 192 columns
 constexpr int TC_M = 128;
-constexpr int TC_STAGES = 5;
+constexpr int TC_STAGES = 5;                 // 5 x 20 KB: two CTAs (and two 256-column TMEM blocks) per SM
 constexpr int TC_PREFETCH = 3;               // stage i+3 refills the slot of MMA i-2
-constexpr int TC_KBYTES = 64;               // K bytes per stage per row
-constexpr int TC_A_BYTES = TC_M * TC_KBYTES;     // 8 KB
-constexpr int TC_B_BYTES = TC_N * TC_KBYTES;     // 12 KB
-constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 40 KB
+constexpr int TC_A_BYTES = TC_M * TC_KBYTES;     // 4 KB
+constexpr int TC_B_BYTES = TC_N * TC_KBYTES;     // 6 KB
+constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 20 KB
+constexpr int TC_SBO = TC_KG * 128;              // bytes between 8-row groups
+constexpr int TC_BCHUNKS = TC_N * TC_KG / 128;   // 16-byte B chunks per producer thread per stage
 constexpr int TC_MAXKB = 256;                                    // k-blocks per parity (<= 189 used)
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 128 + TC_MAXKB * 16 + TC_CELLS * 4;
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 + 256 + TC_MAXKB * 16 + TC_CELLS * 4;
 constexpr int TC_TMEM_COLS = 256;
 constexpr long long TC_WAIT_LIMIT = 1LL << 26;
 
@@ -80,6 +81,7 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+static_assert(TC_KG % 2 == 0, "an MMA consumes two 16-byte k-groups");
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -123,8 +125,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 }
 
 // Warp-specialised pipeline: warp 0 lane 0 issues the MMAs; warps 1..4 (128 producer threads)
-// gather the multipole rows with cp.async and release a stage (fence.proxy.async + arrive on
-// full[s]) TC_PF stages after issuing it; producer thread 0 also moves the two pre-tiled
+// gather the multipole rows with cp.async and release a stage (fence.proxy.async by every
+// lane, one arrive per warp on full[s]) TC_PF stages after issuing it; producer thread 0 also moves the two pre-tiled
 // translation-matrix tiles with TMA bulk copies (expect_tx on full[s]).  tcgen05.commit on
 // empty[s] returns the slot to the producers.  No CTA-wide barrier inside the main loop.
 // Producer release lag.  A stage is released after the producer has issued TC_PF later stages,
@@ -134,7 +136,7 @@ constexpr int TC_PF = 2;
 constexpr int TC_WS_THREADS = 32 + TC_THREADS;  // MMA warp + 4 producer warps
 
 template <bool BF16>
-__global__ void __launch_bounds__(TC_WS_THREADS, 1) k_m2l_tc(TcParams tp)
+__global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 1) k_m2l_tc(TcParams tp)
     uint64_t *full = (uint64_t *)(base + TC_STAGES * TC_STAGE_BYTES);
     uint64_t *empty = full + TC_STAGES;
     uint32_t *tmem_slot = (uint32_t *)(empty + TC_STAGES);
-    int4 *kb_s = (int4 *)(base + TC_STAGES * TC_STAGE_BYTES + 128);
+    int4 *kb_s = (int4 *)(base + TC_STAGES * TC_STAGE_BYTES + 256);
     int *cell_s = (int *)(kb_s + TC_MAXKB);
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 1) k_m2l_tc(TcParams tp)
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_init(smem_u32(&full[s]), TC_THREADS + 1);  // 128 producer arrivals + 1 expect_tx arrival
+            mbar_init(smem_u32(&full[s]), TC_THREADS / 32 + 1);  // one arrival per producer warp + expect_tx
             mbar_init(smem_u32(&empty[s]), 1);              // tcgen05.commit
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -198,10 +200,10 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 1) k_m2l_tc(TcParams tp)
                 unsigned char *st = stages + s * TC_STAGE_BYTES;
                 uint32_t sA = smem_u32(st), sAl = sA + TC_A_BYTES, sB = sAl + TC_A_BYTES, sBl = sB + TC_B_BYTES;
 #pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    uint32_t koff = 256u * ks;
-                    uint64_t dAh = make_desc(sA + koff, 128, 512), dAl = make_desc(sAl + koff, 128, 512);
-                    uint64_t dBh = make_desc(sB + koff, 128, 512), dBl = make_desc(sBl + koff, 128, 512);
+                for (int ks = 0; ks < TC_KG / 2; ++ks) {
+                    uint32_t koff = 256u * ks;  // two 16-byte k-groups per MMA
+                    uint64_t dAh = make_desc(sA + koff, 128, TC_SBO), dAl = make_desc(sAl + koff, 128, TC_SBO);
+                    uint64_t dBh = make_desc(sB + koff, 128, TC_SBO), dBl = make_desc(sBl + koff, 128, TC_SBO);
                     uint32_t acc0 = (i > 0 || ks > 0) ? 1u : 0u;
                     mma_issue<BF16>(tmem, dAh, dBh, idesc, acc0);
                     mma_issue<BF16>(tmem, dAh, dBl, idesc, 1u);
@@ -213,12 +215,13 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 1) k_m2l_tc(TcParams tp)
     } else {
         // ------------------------------- producers ---------------------------------
         const int ptid = tid - 32;
-        int slot_cx[6], slot_cy[6], slot_cz[6], slot_comp[6], slot_kg[6];
+        int slot_cx[TC_BCHUNKS], slot_cy[TC_BCHUNKS], slot_cz[TC_BCHUNKS], slot_comp[TC_BCHUNKS], slot_kg[TC_BCHUNKS];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
+        for (int j = 0; j < TC_BCHUNKS; ++j) {
+            // chunk v sits at byte 16 v: row 8 (v / (8 KG)) + v % 8, k-group (v / 8) % KG
             int v = ptid + TC_THREADS * j;
-            int nrow = 8 * (v >> 5) + (v & 7);
-            slot_kg[j] = (v >> 3) & 3;
+            int nrow = 8 * (v / (8 * TC_KG)) + (v & 7);
+            slot_kg[j] = (v >> 3) % TC_KG;
             int q = nrow / 3;
             slot_comp[j] = nrow - 3 * q;
             int cell = cell_s[q];
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 1) k_m2l_tc(TcParams tp)
                     bulk_g2s(sAl, Alo + ((size_t)kb.x * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
                 }
 #pragma unroll
-                for (int j = 0; j < 6; ++j) {
+                for (int j = 0; j < TC_BCHUNKS; ++j) {
                     int v = ptid + TC_THREADS * j;
                     int sx = (slot_cx[j] + kb.y) & (n - 1);
                     int sy = (slot_cy[j] + kb.z) & (n - 1);
@@ -261,10 +264,12 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 1) k_m2l_tc(TcParams tp)
             }
             cp_async_commit();
             if (i >= TC_PF) {
-                // this thread's copies of stage i - TC_PF have landed: publish them
+                // this thread's copies of stage i - TC_PF have landed: make them visible to the
+                // async proxy, then one lane publishes the warp's share of the stage
                 cp_async_wait<TC_PF>();
                 fence_proxy_async();
-                mbar_arrive(smem_u32(&full[(i - TC_PF) % TC_STAGES]));
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(smem_u32(&full[(i - TC_PF) % TC_STAGES]));
             }
         }
         cp_async_wait<0>();

@@ -17,6 +17,9 @@ constexpr int MAX_DEPTH = 8;      // deepest octree level
 constexpr int LEAF_SORT_CAP = 4096;  // per-leaf sort capacity (32 KB of 64-bit keys)
 constexpr int OUT_ROWS = 128;     // rows of every packed translation matrix (output coefficients, padded)
 constexpr int NT = 343;           // M2L offsets t in [-3,3]^3
+constexpr int TC_KBYTES = 32;     // tensor-core M2L: K bytes of one pipeline stage per operand row
+constexpr int TC_KG = TC_KBYTES / 16;   // 16-byte k-groups per stage
+constexpr int TC_A_TILE = 128 * TC_KBYTES;  // bytes of one translation-matrix tile (128 rows)
 
 // device error word bits
 constexpr int ERRBIT_LEAF_OVERFLOW = 1;
