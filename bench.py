@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--k0", type=int, default=4)
     ap.add_argument("--m2l", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--periodic-levels", type=int, default=2)
+    ap.add_argument("--rho-cut", type=float, default=5.0,
+                    help="pairs closer than rho_cut sigma take the smoothed kernel, farther ones the singular")
     ap.add_argument("--check", type=int, default=16, help="sampled targets for the oracle error (0 = off)")
     ap.add_argument("--cpu-targets", type=int, default=0, help="oracle targets for cpu_baseline (0 = one per host core)")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -121,10 +123,12 @@ def combine_ranks(ms, particles, steps, device=None):
     return ms_max, ws * particles * steps / (ms_max / 1e3)
 
 
-def p2p_work(x, L, depth, R, sigma):
+def p2p_work(x, L, depth, R, sigma, Rc=0, rho_cut=6.0):
     """Pairs the P2P visits, split as the kernel splits them: by the gap d between the target
-    leaf's box and each source octant's box, d < 6.5 sigma -> smoothed kernel (61 flops),
-    d >= 6.5 sigma -> singular kernel (42 flops).  Returns (pairs, flops)."""
+    leaf's box and each source octant's box.  In the R near rings d < 6.5 sigma -> smoothed
+    kernel (61 flops), d >= 6.5 sigma -> singular kernel (42 flops); in the rings R+1..Rc
+    (Gaussian-tail correction of the far field) d < rho_cut sigma -> smoothed minus singular
+    (61 flops), farther octants are skipped.  Returns (pairs, flops)."""
     import itertools
     import numpy as np
     ns = 1 << depth
@@ -157,9 +161,11 @@ def p2p_work(x, L, depth, R, sigma):
     ohi = ohi.reshape(ns, ns, ns, 8, 3)
     g = np.arange(ns)
     C = np.meshgrid(g, g, g, indexing="ij")
-    d2_sing = 42.25 * sigma * sigma
+    d2_sing = np.float32(42.25 * sigma * sigma)
+    d2_cut = np.float32(rho_cut * rho_cut * sigma * sigma)
     p_s, p_g = 0.0, 0.0
-    for t in itertools.product(range(-R, R + 1), repeat=3):
+    for t in itertools.product(range(-max(R, Rc), max(R, Rc) + 1), repeat=3):
+        corr = max(abs(v) for v in t) > R
         nb = [C[d] + t[d] for d in range(3)]
         sh = [np.floor_divide(nb[d], ns) * L for d in range(3)]
         ix = [np.mod(nb[d], ns) for d in range(3)]
@@ -171,6 +177,9 @@ def p2p_work(x, L, depth, R, sigma):
             gap = np.maximum(0.0, np.maximum(slo - hi[..., d][..., None], lo[..., d][..., None] - shi))
             d2 += gap * gap
         pairs = cnt[..., None] * cn
+        if corr:
+            p_s += float(pairs[d2 < d2_cut].sum())
+            continue
         sing = d2 >= d2_sing
         p_g += float(pairs[sing].sum())
         p_s += float(pairs[~sing].sum())
@@ -266,13 +275,13 @@ def run_timestep(args):
     N = n ** 3
     f = wl.make_vortex_lattice(n, args.k0, 1)
     nu = wl.viscosity_for_re_lambda(n, args.k0, 1, 100.0)
-    out = {"metric": "Heun step and reinitialisation time at %d^3" % n, "unit": "ms", "nu": nu, "rho_cut": 5.0,
+    out = {"metric": "Heun step and reinitialisation time at %d^3" % n, "unit": "ms", "nu": nu, "rho_cut": args.rho_cut,
            "dt": 0.01, "steps": 10, "reinit_iterations": 20, "runs": {}}
     for m2l in ("bf16x3", "fp32"):
         X = torch.tensor(f["x"], dtype=torch.float32, device="cuda")
         G = torch.tensor(f["alpha"], dtype=torch.float32, device="cuda")
-        # rho_cut = 5 keeps 4h leaves with two near rings up to sigma = 1.6 h (1 - q(5) = 1.5e-5)
-        h = vf.VortexFMM(p=args.p, periodic_levels=args.periodic_levels, m2l=m2l, rho_cut=5.0)
+        # rho_cut = 5 keeps 4h leaves within two rings up to sigma = 1.6 h (1 - q(5) = 1.5e-5)
+        h = vf.VortexFMM(p=args.p, periodic_levels=args.periodic_levels, m2l=m2l, rho_cut=args.rho_cut)
         d0 = h.diagnostics(X, G)
         sigma = f["sigma"]
         sigma = h.rk_step(X, G, sigma, 0.01, nu)  # warm-up step
@@ -331,7 +340,7 @@ def main():
     G = torch.tensor(f["alpha"], dtype=torch.float32, device=dev)
     U = torch.empty_like(G)
     S = torch.empty_like(G)
-    h = vf.VortexFMM(p=args.p, periodic_levels=args.periodic_levels, m2l=args.m2l)
+    h = vf.VortexFMM(p=args.p, periodic_levels=args.periodic_levels, m2l=args.m2l, rho_cut=args.rho_cut)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -387,8 +396,8 @@ def main():
 
     # roofline of the dominant kernel (P2P): FP32 ALU bound
     p2p_ms = statistics.mean(p["p2p"] for p in phase_ms)
-    R = info["near_rings"]
-    pairs, flops = p2p_work(f["x"], 2 * math.pi, info["depth"], R, sigma)
+    R, Rc = info["near_rings"], info["correction_rings"]
+    pairs, flops = p2p_work(f["x"], 2 * math.pi, info["depth"], R, sigma, Rc, args.rho_cut)
     achieved = flops / (p2p_ms / 1e3) / 1e12
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -401,7 +410,7 @@ def main():
         import oracle
         tid = wl.target_subset(N, args.check, seed=3)
         uo, so = oracle.direct(f["x"], f["alpha"], sigma, K=1, targets=tid)
-        h0 = vf.VortexFMM(p=args.p, periodic_levels=0, m2l=args.m2l)
+        h0 = vf.VortexFMM(p=args.p, periodic_levels=0, m2l=args.m2l, rho_cut=args.rho_cut)
         h0.build_tree(X)
         u0, s0 = h0.eval(G, sigma)
         h0.sync()
@@ -423,6 +432,7 @@ def main():
         "config": {"workload": "vortex lattice %d^3 (%d particles), k0=%d, sigma=h, p=%d, 27^3 periodic images"
                    % (n, N, args.k0, args.p), "n_particles": N, "p": args.p, "m2l": args.m2l,
                    "periodic_levels": args.periodic_levels, "depth": info["depth"], "near_rings": R,
+                   "correction_rings": Rc, "rho_cut": args.rho_cut,
                    "l2": "inputs (x, gamma 402 MB) larger than L2; no flush",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -73,8 +73,14 @@ typedef struct vfmm_config {
     int p;               /* expansion order: degrees 0..p, (p+1)^2 coefficients (Eq. fmm3dm); 2 <= p <= 10 */
     int depth;           /* leaf depth D of the uniform octree; 0 = choose from ncrit */
     int ncrit;           /* target mean particles per leaf when depth == 0 */
-    int near_rings;      /* R: near field = (2R+1)^3 leaves; 0 = smallest R with R w >= rho_cut sigma; R <= 2 */
-    double rho_cut;      /* far-field pairs must satisfy |r| >= rho_cut sigma (default 6) */
+    int near_rings;      /* R: near field = (2R+1)^3 leaves with the smoothed kernel; 0 = automatic: 1 for the
+                          * FP32 velocity / stretching evaluation, else the smallest R with R w >= rho_cut sigma.
+                          * Where R w < rho_cut sigma <= 2 w in FP32 (not the gradient), ring 2 is left to the
+                          * M2L and the source octants of ring 2 closer than rho_cut sigma get the smoothed-
+                          * minus-singular correction pair by pair, so every pair closer than rho_cut sigma
+                          * still takes the smoothed kernel.  R <= 2; rho_cut sigma > 2 w is an error. */
+    double rho_cut;      /* pairs farther apart than rho_cut sigma may take the singular kernel (default 5:
+                          * 1 - q(5) = 1.5e-5) */
     int periodic_levels; /* S: image cube of 3^(S+1) boxes per side; 0 = the 27 central boxes only */
     double box;          /* L, the period (default 2 pi) */
     int dtype;           /* VFMM_F32 | VFMM_F64 */
@@ -86,7 +92,7 @@ typedef struct vfmm_config {
 
 typedef struct vfmm_ctx *vfmm_handle;
 
-/* Fill *cfg with defaults: p=10, depth=0, ncrit=64, near_rings=0, rho_cut=6, S=2, L=2 pi,
+/* Fill *cfg with defaults: p=10, depth=0, ncrit=64, near_rings=0, rho_cut=5, S=2, L=2 pi,
  * F32, M2L BF16X3, FMM, K=1, stream NULL. */
 int vfmm_config_default(vfmm_config *cfg);
 
@@ -180,7 +186,9 @@ int vfmm_get_timings(vfmm_handle h, double *ms_per_phase, int nphase);
 
 /* Tree facts: out[0] = depth D, out[1] = near rings R used by the last evaluation,
  * out[2] = leaves per side, out[3] = maximum particles in one leaf, out[4] = particles,
- * out[5] = CUDA kernels launched by the last vfmm_build_tree plus the evaluations since. */
+ * out[5] = CUDA kernels launched by the last vfmm_build_tree plus the evaluations since,
+ * out[6] = outer ring of the Gaussian-tail correction in the last evaluation (0 = none).
+ * Writes min(nout, 7) values. */
 int vfmm_get_tree_info(vfmm_handle h, int64_t *out, int nout);
 
 /* Largest n accepted by vfmm_direct_eval_noalloc. */

@@ -17,7 +17,7 @@ PRECISIONS = {"fp32": _native.VFMM_M2L_FP32, "fp64": _native.VFMM_M2L_FP64,
 PHASES = ["tree", "p2m", "m2m", "m2l", "periodic", "l2l", "l2p", "p2p"]
 
 
-def make_config(p=10, depth=0, ncrit=64, near_rings=0, rho_cut=6.0, periodic_levels=2,
+def make_config(p=10, depth=0, ncrit=64, near_rings=0, rho_cut=5.0, periodic_levels=2,
                 box=2 * math.pi, dtype="f32", m2l="bf16x3", method="fmm", direct_images=1,
                 stream=None):
     c = config_default()

@@ -176,7 +176,7 @@ def vfmm_get_timings(h):
 
 
 def vfmm_get_tree_info(h):
-    buf = (ctypes.c_int64 * 6)()
-    check(lib().vfmm_get_tree_info(h, buf, 6), "vfmm_get_tree_info", h)
+    buf = (ctypes.c_int64 * 7)()
+    check(lib().vfmm_get_tree_info(h, buf, 7), "vfmm_get_tree_info", h)
     return {"depth": buf[0], "near_rings": buf[1], "leaves_per_side": buf[2],
-            "max_leaf": buf[3], "n": buf[4], "launches": buf[5]}
+            "max_leaf": buf[3], "n": buf[4], "launches": buf[5], "correction_rings": buf[6]}

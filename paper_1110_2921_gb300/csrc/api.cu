@@ -231,20 +231,26 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
     if (!gamma || !u_out) return fail(c, VFMM_ERR_ARG, "null gamma or u_out");
     if (!std::isfinite(sigma) || sigma <= 0.0) return fail(c, VFMM_ERR_ARG, "sigma must be finite and > 0");
     const bool fmm = c->cfg.method == VFMM_METHOD_FMM;
-    int R;
+    // Every pair closer than rho_cut sigma takes the smoothed kernel: Rreq rings of leaves
+    // cover them.  The FP32 velocity / stretching path keeps one ring in the near field and
+    // gives the second ring to the M2L, adding there the smoothed-minus-singular correction
+    // for the source octants that come within rho_cut sigma; FP64 and the gradient path
+    // take all Rreq rings in the near field.
+    int R, Rc = 0;
     if (fmm) {
-        R = c->cfg.near_rings;
-        if (R <= 0) {
-            R = 1;
-            while (R * c->leaf_w < c->cfg.rho_cut * sigma && R < 3) ++R;
-        }
-        if (R > 2)
+        int Rreq = 1;
+        while (Rreq * c->leaf_w < c->cfg.rho_cut * sigma && Rreq < 3) ++Rreq;
+        if (Rreq > 2)
             return fail(c, VFMM_ERR_UNSUPPORTED,
                         "the near field would need more than 2 rings of leaves (rho_cut * sigma > 2 * leaf width); use a shallower tree");
+        const bool corr_ok = !c->f64 && !grad;
+        R = c->cfg.near_rings > 0 ? c->cfg.near_rings : (corr_ok ? 1 : Rreq);
+        if (corr_ok && Rreq > R) Rc = Rreq;
     } else {
         R = c->cfg.direct_images;
     }
     c->last_R = R;
+    c->last_Rc = Rc;
     cudaStream_t st = c->stream;
     int rc;
     cudaEventRecord(c->ev[2], st);
@@ -335,7 +341,7 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
     if (grad) {
         if ((rc = launch_p2p_grad(c, R, sigma, uf, sf, u_out, s_out, fmm ? -1 : c->cfg.direct_images))) return rc;
     } else {
-        if ((rc = launch_p2p(c, R, sigma, uf, sf, u_out, s_out, fmm ? -1 : c->cfg.direct_images))) return rc;
+        if ((rc = launch_p2p(c, R, Rc, sigma, uf, sf, u_out, s_out, fmm ? -1 : c->cfg.direct_images))) return rc;
     }
     cudaEventRecord(c->ev[9], st);
     c->timed_eval = true;
@@ -429,7 +435,7 @@ int vfmm_config_default(vfmm_config *cfg)
     cfg->depth = 0;
     cfg->ncrit = 64;
     cfg->near_rings = 0;
-    cfg->rho_cut = 6.0;
+    cfg->rho_cut = 5.0;
     cfg->periodic_levels = 2;
     cfg->box = 6.283185307179586477;
     cfg->dtype = VFMM_F32;
@@ -700,8 +706,8 @@ int vfmm_get_tree_info(vfmm_handle h, int64_t *out, int nout)
 {
     if (!h || !out) return VFMM_ERR_ARG;
     Ctx *c = &h->c;
-    int64_t v[6] = {c->depth, c->last_R, c->nside, c->max_leaf, c->n, c->launches};
-    for (int i = 0; i < nout && i < 6; ++i) out[i] = v[i];
+    int64_t v[7] = {c->depth, c->last_R, c->nside, c->max_leaf, c->n, c->launches, c->last_Rc};
+    for (int i = 0; i < nout && i < 7; ++i) out[i] = v[i];
     return VFMM_OK;
 }
 

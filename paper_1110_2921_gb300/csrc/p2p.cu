@@ -130,6 +130,7 @@ struct P3Const {
     float ks, fs;      // series prefactors sqrt(2/pi)/(sigma s)^3 and /(sigma s)^5
     float d2_series;   // leaf-box squared gap (true units) below which rho < 0.5 may occur
     float d2_singular; // leaf-box squared gap (true units) above which rho >= 6.5
+    float d2_cut;      // (rho_cut sigma)^2: beyond the near rings, octants closer than this are corrected
     float L;
 };
 
@@ -144,7 +145,18 @@ __device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, fl
     float dx = xi0 - xj.x, dy = xi1 - xj.y, dz = xi2 - xj.z;
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     float K, F;
-    if (MODE == 2) {  // singular kernel: K = 1/r^3, F = -3/r^5
+    if (MODE == 3) {  // smoothed minus singular: the far field's missing Gaussian tail
+        float e = ex2_approx(-r2);
+        float rinv = rsqrt_approx(r2);
+        float r = r2 * rinv;
+        float t = rcp_approx(fmaf(r, k.ct, 1.0f));
+        float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                              0.254829592f);
+        float omq = e * fmaf(k.cq, r, poly);  // 1 - q(rho)
+        float rinv2 = rinv * rinv;
+        K = -omq * (rinv2 * rinv);
+        F = rinv2 * fmaf(-3.0f, K, k.cf * e);
+    } else if (MODE == 2) {  // singular kernel: K = 1/r^3, F = -3/r^5
         float rinv = rsqrt_approx(r2);
         float rinv2 = rinv * rinv;
         K = rinv2 * rinv;
@@ -272,7 +284,7 @@ __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict
                                                         const int *__restrict__ ls, const float4 *__restrict__ bbox,
                                                         const int *__restrict__ oct_start,
                                                         const float4 *__restrict__ oct_box, int nside, int log2n,
-                                                        int R, int direct_K, float leaf_w, P3Const kc,
+                                                        int R, int Rc, int direct_K, float leaf_w, P3Const kc,
                                                         const float *__restrict__ ufar, const float *__restrict__ sfar,
                                                         const int *__restrict__ perm, float *__restrict__ u_out,
                                                         float *__restrict__ s_out)
@@ -309,18 +321,25 @@ __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict
         // (2K+1)^3 image boxes
         int lo[3], hi[3];
         const int cc[3] = {cx, cy, cz};
+        // the near rings R (full smoothed kernel) and, out to Rc, the correction rings; for the
+        // direct sum every leaf of the (2K+1)^3 image boxes
+        const int Rl = direct_K >= 0 ? 0 : (Rc > R ? Rc : R);
         for (int d = 0; d < 3; ++d) {
-            lo[d] = direct_K >= 0 ? -cc[d] - direct_K * nside : -R;
-            hi[d] = direct_K >= 0 ? nside - 1 - cc[d] + direct_K * nside : R;
+            lo[d] = direct_K >= 0 ? -cc[d] - direct_K * nside : -Rl;
+            hi[d] = direct_K >= 0 ? nside - 1 - cc[d] + direct_K * nside : Rl;
         }
         for (int ox = lo[0]; ox <= hi[0]; ++ox)
             for (int oy = lo[1]; oy <= hi[1]; ++oy)
                 for (int oz = lo[2]; oz <= hi[2]; ++oz) {
+                    const bool corr = direct_K < 0 && (abs(ox) > R || abs(oy) > R || abs(oz) > R);
                     int nx = cx + ox, ny = cy + oy, nz = cz + oz;
                     int sl = ((nx & (nside - 1)) * nside + (ny & (nside - 1))) * nside + (nz & (nside - 1));
                     float shx = kc.L * (float)(nx >> log2n), shy = kc.L * (float)(ny >> log2n), shz = kc.L * (float)(nz >> log2n);
                     // closest approach of the target leaf box and each source octant box selects
-                    // the inner loop for that octant (warp-uniform)
+                    // the inner loop for that octant (warp-uniform): in the near rings smoothed
+                    // (with or without the small-rho series) or singular; beyond them, the
+                    // Gaussian-tail correction for octants closer than rho_cut sigma (mode 3),
+                    // nothing otherwise (mode 4, the M2L has them)
                     int modes = 0;
 #pragma unroll
                     for (int o = 0; o < 8; ++o) {
@@ -329,9 +348,11 @@ __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict
                         float gy = fmaxf(0.f, fmaxf(slo.y + shy - thi.y, tlo.y - shi.y - shy));
                         float gz = fmaxf(0.f, fmaxf(slo.z + shz - thi.z, tlo.z - shi.z - shz));
                         float d2 = gx * gx + gy * gy + gz * gz;
-                        int mode = d2 >= kc.d2_singular ? 2 : (d2 >= kc.d2_series ? 1 : 0);
-                        modes |= mode << (2 * o);
+                        int mode = corr ? (d2 < kc.d2_cut ? 3 : 4)
+                                        : (d2 >= kc.d2_singular ? 2 : (d2 >= kc.d2_series ? 1 : 0));
+                        modes |= mode << (3 * o);
                     }
+                    if (corr && modes == 04444444444) continue;  // all eight octants are far: nothing to add
                     // sources relative to the target leaf centre, with the image shift
                     float ox0 = shx - zx, ox1 = shy - zy, ox2 = shz - zz;
                     int sb = ls[sl], se = ls[sl + 1];
@@ -353,14 +374,15 @@ __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict
                         // runs of consecutive octants with the same inner loop
                         int o = 0;
                         while (o < 8) {
-                            const int mode = (modes >> (2 * o)) & 3;
+                            const int mode = (modes >> (3 * o)) & 7;
                             int o2 = o + 1;
-                            while (o2 < 8 && ((modes >> (2 * o2)) & 3) == mode) ++o2;
+                            while (o2 < 8 && ((modes >> (3 * o2)) & 7) == mode) ++o2;
                             int j0 = max(ost[o], c0) - c0, j1 = min(ost[o2], c1) - c0;
                             if (j0 < j1) {
                                 if (mode == 2) tile3<2>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
                                 else if (mode == 1) tile3<1>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
-                                else tile3<0>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
+                                else if (mode == 0) tile3<0>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
+                                else if (mode == 3) tile3<3>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
                             }
                             o = o2;
                         }
@@ -459,7 +481,7 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p_f64(const dvec4 *__restrict__ xs
     }
 }
 
-int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, void *u_out, void *s_out,
+int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void *sfar, void *u_out, void *s_out,
                int direct_K)
 {
     int log2n = 0;
@@ -489,6 +511,7 @@ int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, 
         kc.fs = (float)(cpi / (ss * ss * ss * ss * ss));
         kc.d2_series = (float)(0.36 * sigma * sigma);      // (0.6 sigma)^2: margin over rho = 0.5
         kc.d2_singular = (float)(42.25 * sigma * sigma);   // (6.5 sigma)^2
+        kc.d2_cut = (float)(c->cfg.rho_cut * c->cfg.rho_cut * sigma * sigma);
         kc.L = (float)c->cfg.box;
         const int per_block = P3_THREADS * P3_TPT;
         int chunks3 = (c->max_leaf + per_block - 1) / per_block;
@@ -498,7 +521,7 @@ int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, 
         k_p2p_f32<<<grid3, P3_THREADS, 0, c->stream>>>((const float4 *)c->xs.p, (const float4 *)c->gs.p,
                                                        (const int *)c->leaf_start.p, (const float4 *)c->bbox.p,
                                                        (const int *)c->oct_start.p, (const float4 *)c->oct_box.p,
-                                                       c->nside, log2n, R, direct_K, (float)c->leaf_w, kc,
+                                                       c->nside, log2n, R, Rc, direct_K, (float)c->leaf_w, kc,
                                                        (const float *)ufar, (const float *)sfar, (const int *)c->perm.p,
                                                        (float *)u_out, (float *)s_out);
     }

@@ -81,6 +81,7 @@ struct Ctx {
     int64_t nleaf = 1;
     int max_leaf = 0;
     int last_R = 0;
+    int last_Rc = 0;  // outer ring of the Gaussian-tail correction (0: none)
     bool built = false;
     double leaf_w = 0.0;
 
@@ -127,7 +128,7 @@ int launch_p2p_grad(Ctx *c, int R, double sigma, const void *ufar, const void *g
                     int direct_K);
 int launch_adjoint_combine(Ctx *c, const void *G1, const void *w, const void *G2, const void *gamma, void *dx);
 // direct_K >= 0: direct sum over every leaf of the (2K+1)^3 image boxes; -1: the FMM near field (R rings)
-int launch_p2p(Ctx *c, int R, double sigma, const void *ufar, const void *sfar, void *u_out,
+int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void *sfar, void *u_out,
                void *s_out, int direct_K);
 int launch_tc_m2l(Ctx *c, int level, const int4 *kb_dev, const int *kb_off, const int *kb_cnt, bool bf16);
 int launch_split(Ctx *c, int level, bool bf16);

@@ -23,7 +23,8 @@ def test_bench_workload_256cubed_sampled():
     tid = wl.target_subset(256 ** 3, 12, seed=3)
     uo, so = oracle.direct(f["x"], f["alpha"], f["sigma"], K=1, targets=tid)
     u, s, info = run_fmm(f["x"], f["alpha"], f["sigma"], p=10, periodic_levels=0, m2l="bf16x3")
-    assert info["depth"] == 6 and info["near_rings"] == 2
+    # one near ring; the second ring goes to the M2L with the Gaussian-tail correction
+    assert info["depth"] == 6 and info["near_rings"] == 1 and info["correction_rings"] == 2
     eu, es = rel_l2(u[tid], uo), rel_l2(s[tid], so)
     print("256^3 sampled: u %.3e S %.3e" % (eu, es))
     assert eu < 1e-4 and es < 1e-3
@@ -82,7 +83,7 @@ def test_overlap_and_precision_128cubed(ratio):
 
 
 def test_reduced_cutoff_with_spread_cores_128cubed():
-    # rho_cut = 5 (the time-step setting): cores spread to 1.5 h stay on 4h leaves with R = 2;
+    # rho_cut = 5 (the time-step setting): cores spread to 1.5 h stay on 4h leaves within two rings;
     # the dropped smoothing tail 1 - q(5) = 1.5e-5 keeps the p = 10 accuracy
     f = wl.make_vortex_lattice(128, 4, 1, sigma_over_h=1.5)
     tid = wl.target_subset(128 ** 3, 24, seed=3)
@@ -90,5 +91,5 @@ def test_reduced_cutoff_with_spread_cores_128cubed():
     u, s, info = run_fmm(f["x"], f["alpha"], f["sigma"], p=10, rho_cut=5.0, periodic_levels=0, m2l="bf16x3")
     eu, es = rel_l2(u[tid], uo), rel_l2(s[tid], so)
     print("rho_cut=5 sigma/h=1.5 depth=%d R=%d: u %.3e S %.3e" % (info["depth"], info["near_rings"], eu, es))
-    assert info["depth"] == 5 and info["near_rings"] == 2
+    assert info["depth"] == 5 and info["near_rings"] == 1 and info["correction_rings"] == 2
     assert eu < 1e-4 and es < 1e-3

@@ -78,8 +78,9 @@ def test_fmm_fp64_order_convergence(field16, oracle16_k1, p, request):
 
 
 def test_fmm_fp32_matches_fp64_fmm(field16):
+    # the same tree and lists in both precisions: two smoothed near rings, no correction
     f = field16
-    kw = dict(method="fmm", p=10, depth=2, periodic_levels=1)
+    kw = dict(method="fmm", p=10, depth=2, periodic_levels=1, near_rings=2)
     u64, s64, _ = run_fmm(f["x"], f["alpha"], f["sigma"], dtype="f64", **kw)
     u32, s32, _ = run_fmm(f["x"], f["alpha"], f["sigma"], dtype="f32", m2l="fp32", **kw)
     assert rel_l2(u32, u64) < 2e-5
@@ -151,3 +152,28 @@ def test_errors_reported():
         assert e.value.status == -1
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("sigma_over_h", [1.0, 1.4])
+def test_ring_two_correction_off_lattice(sigma_over_h):
+    # jittered positions and wide cores: ring-2 pairs reach rho ~ 2, where the singular kernel of
+    # the M2L misses a large part of the smoothed one; the correction pairs must restore it
+    f = wl.make_vortex_lattice(32, 4, 1)
+    h = 2 * np.pi / 32
+    x = wl.jitter(f["x"], h, 0.45, seed=5)
+    sigma = sigma_over_h * f["sigma"]
+    tid = wl.target_subset(32 ** 3, 256, seed=3)
+    uo, so = oracle.direct(x, f["alpha"], sigma, K=1, targets=tid)
+    u, s, info = run_fmm(x, f["alpha"], sigma, p=10, depth=3, periodic_levels=0, m2l="bf16x3", rho_cut=5.0)
+    assert info["near_rings"] == 1 and info["correction_rings"] == 2
+    eu, es = rel_l2(u[tid], uo), rel_l2(s[tid], so)
+    print("sigma/h=%.1f: u %.3e S %.3e" % (sigma_over_h, eu, es))
+    assert eu < 1e-4 and es < 1e-3
+    if sigma_over_h > 1.2:
+        # without the correction (rho_cut sigma within one leaf width: one ring, no correction
+        # pairs) the same evaluation misses the ring-2 Gaussian tail
+        u1, s1, info1 = run_fmm(x, f["alpha"], sigma, p=10, depth=3, periodic_levels=0, m2l="bf16x3", rho_cut=2.8)
+        assert info1["near_rings"] == 1 and info1["correction_rings"] == 0
+        eu1, es1 = rel_l2(u1[tid], uo), rel_l2(s1[tid], so)
+        print("uncorrected: u %.3e S %.3e" % (eu1, es1))
+        assert eu1 > 3 * eu and es1 > 3 * es
