@@ -131,6 +131,7 @@ struct P3Const {
     float d2_series;   // leaf-box squared gap (true units) below which rho < 0.5 may occur
     float d2_singular; // leaf-box squared gap (true units) above which rho >= 6.5
     float d2_cut;      // (rho_cut sigma)^2: beyond the near rings, octants closer than this are corrected
+    float w2_lo;       // leaf width squared, less a rounding margin
     float L;
 };
 
@@ -195,21 +196,53 @@ __device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, fl
     a.E2 = fmaf(f, cj.z, a.E2);
 }
 
+// Tuning: P3_SPLIT groups of lanes hold the same P3_TPT targets each and split the sources
+// between them (partial sums combined by shuffles at the end).
+#ifndef VFMM_P3_SPLIT
+#define VFMM_P3_SPLIT 1
+#endif
+#ifndef VFMM_P3_TPT
+#define VFMM_P3_TPT 2
+#endif
+#ifndef VFMM_P3_UNROLL
+#define VFMM_P3_UNROLL 2
+#endif
 constexpr int P3_THREADS = 32;   // one warp per target leaf chunk
-constexpr int P3_TPT = 2;        // targets per thread
+constexpr int P3_SPLIT = VFMM_P3_SPLIT;
+constexpr int P3_GROUP = P3_THREADS / P3_SPLIT;  // lanes per source group
+constexpr int P3_TPT = VFMM_P3_TPT;              // targets per thread
+constexpr int P3_TARGETS = P3_GROUP * P3_TPT;    // targets per block
 constexpr int P3_TILE = 64;      // staged sources
+constexpr int P3_UNROLL = VFMM_P3_UNROLL;
+static_assert(P3_SPLIT == 1 || P3_SPLIT == 2, "one or two source groups");
+
+// one staged source: scaled position relative to the target leaf centre, strength, and
+// c = gamma x x (the cross product the velocity sum needs, formed once per source)
+struct __align__(16) Src3 {
+    float4 x, g, c;
+};
 
 template <int MODE>
 __device__ __forceinline__ void tile3(const P3Const &k, const float (&xi)[P3_TPT][3], const float (&gi)[P3_TPT][3],
-                                      const float4 *sx, const float4 *sg, const float4 *sc, int j0, int j1,
-                                      Acc3 (&acc)[P3_TPT])
+                                      const Src3 *src, int j0, int j1, Acc3 (&acc)[P3_TPT])
 {
-#pragma unroll 2
-    for (int j = j0; j < j1; ++j) {
-        float4 xj = sx[j], gj = sg[j], cj = sc[j];
+    // source group h takes the sources j0 + h, j0 + h + P3_SPLIT, ...
+    const int h = P3_SPLIT == 1 ? 0 : (int)(threadIdx.x / P3_GROUP);
+#pragma unroll P3_UNROLL
+    for (int j = j0 + h; j < j1; j += P3_SPLIT) {
+        const float4 xj = src[j].x, gj = src[j].g, cj = src[j].c;
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) pair3<MODE>(k, xi[q][0], xi[q][1], xi[q][2], gi[q][0], gi[q][1], gi[q][2], xj, gj, cj, acc[q]);
     }
+}
+
+// sum of the source groups' partial sums (every group ends with the total)
+__device__ __forceinline__ void reduce_groups(Acc3 &a)
+{
+    if (P3_SPLIT == 1) return;
+    float *v = reinterpret_cast<float *>(&a);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], P3_GROUP);
 }
 
 struct AccD {
@@ -289,7 +322,7 @@ __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict
                                                         const int *__restrict__ perm, float *__restrict__ u_out,
                                                         float *__restrict__ s_out)
 {
-    __shared__ float4 sx[P3_TILE], sg[P3_TILE], sc[P3_TILE];
+    __shared__ Src3 src[P3_TILE];
     __shared__ int ost[9];
     const int leaf = blockIdx.x;
     const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
@@ -297,13 +330,13 @@ __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict
     const float zx = (cx + 0.5f) * leaf_w, zy = (cy + 0.5f) * leaf_w, zz = (cz + 0.5f) * leaf_w;
     const float s = kc.s;
     const float4 tlo = bbox[2 * leaf], thi = bbox[2 * leaf + 1];
-    const int per_block = P3_THREADS * P3_TPT;
-    for (int t0 = tb + blockIdx.y * per_block; t0 < te; t0 += gridDim.y * per_block) {
+    const int hl = threadIdx.x % P3_GROUP, grp = threadIdx.x / P3_GROUP;
+    for (int t0 = tb + blockIdx.y * P3_TARGETS; t0 < te; t0 += gridDim.y * P3_TARGETS) {
         float xi[P3_TPT][3], gi[P3_TPT][3];
         int tix[P3_TPT];
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) {
-            int ti = t0 + threadIdx.x + q * P3_THREADS;
+            int ti = t0 + hl + q * P3_GROUP;
             tix[q] = ti;
             float4 x = ti < te ? xs[ti] : make_float4(zx, zy, zz, 0.f);
             float4 g = ti < te ? gs[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -332,6 +365,13 @@ __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict
             for (int oy = lo[1]; oy <= hi[1]; ++oy)
                 for (int oz = lo[2]; oz <= hi[2]; ++oz) {
                     const bool corr = direct_K < 0 && (abs(ox) > R || abs(oy) > R || abs(oz) > R);
+                    if (corr) {
+                        // the cells alone keep a leaf |o| rings away at least (|o| - 1) w apart
+                        // along that axis: skip the leaves that cannot come within rho_cut sigma
+                        float gx = (float)max(abs(ox) - 1, 0), gy = (float)max(abs(oy) - 1, 0),
+                              gz = (float)max(abs(oz) - 1, 0);
+                        if ((gx * gx + gy * gy + gz * gz) * kc.w2_lo >= kc.d2_cut) continue;
+                    }
                     int nx = cx + ox, ny = cy + oy, nz = cz + oz;
                     int sl = ((nx & (nside - 1)) * nside + (ny & (nside - 1))) * nside + (nz & (nside - 1));
                     float shx = kc.L * (float)(nx >> log2n), shy = kc.L * (float)(ny >> log2n), shz = kc.L * (float)(nz >> log2n);
@@ -365,9 +405,9 @@ __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict
                         for (int j = threadIdx.x; j < cnt; j += P3_THREADS) {
                             float4 x = xs[s0 + j], g = gs[s0 + j];
                             float a0 = s * (x.x + ox0), a1 = s * (x.y + ox1), a2 = s * (x.z + ox2);
-                            sx[j] = make_float4(a0, a1, a2, 0.f);
-                            sg[j] = g;
-                            sc[j] = make_float4(g.y * a2 - g.z * a1, g.z * a0 - g.x * a2, g.x * a1 - g.y * a0, 0.f);
+                            src[j].x = make_float4(a0, a1, a2, 0.f);
+                            src[j].g = g;
+                            src[j].c = make_float4(g.y * a2 - g.z * a1, g.z * a0 - g.x * a2, g.x * a1 - g.y * a0, 0.f);
                         }
                         __syncwarp();
                         const int c0 = s0 - sb, c1 = c0 + cnt;
@@ -379,21 +419,24 @@ __global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict
                             while (o2 < 8 && ((modes >> (3 * o2)) & 7) == mode) ++o2;
                             int j0 = max(ost[o], c0) - c0, j1 = min(ost[o2], c1) - c0;
                             if (j0 < j1) {
-                                if (mode == 2) tile3<2>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
-                                else if (mode == 1) tile3<1>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
-                                else if (mode == 0) tile3<0>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
-                                else if (mode == 3) tile3<3>(kc, xi, gi, sx, sg, sc, j0, j1, acc);
+                                if (mode == 2) tile3<2>(kc, xi, gi, src, j0, j1, acc);
+                                else if (mode == 1) tile3<1>(kc, xi, gi, src, j0, j1, acc);
+                                else if (mode == 0) tile3<0>(kc, xi, gi, src, j0, j1, acc);
+                                else if (mode == 3) tile3<3>(kc, xi, gi, src, j0, j1, acc);
                             }
                             o = o2;
                         }
                     }
                 }
-        // u = s^2 (A x x^ - U), S = s^3 (A x gamma + D x x^ - E), times 1/(4 pi)
+        // u = s^2 (A x x^ - U), S = s^3 (A x gamma + D x x^ - E), times 1/(4 pi); source group
+        // h writes its share of the targets
         const float su = INV_4PI_F * s * s, ss = su * s;
+#pragma unroll
+        for (int q = 0; q < P3_TPT; ++q) reduce_groups(acc[q]);
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) {
             int ti = tix[q];
-            if (ti >= te) continue;
+            if (ti >= te || (q * P3_SPLIT) / P3_TPT != grp) continue;
             const Acc3 &a = acc[q];
             const float *x = xi[q], *g = gi[q];
             float u0 = su * (a.A1 * x[2] - a.A2 * x[1] - a.U0);
@@ -512,9 +555,9 @@ int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void
         kc.d2_series = (float)(0.36 * sigma * sigma);      // (0.6 sigma)^2: margin over rho = 0.5
         kc.d2_singular = (float)(42.25 * sigma * sigma);   // (6.5 sigma)^2
         kc.d2_cut = (float)(c->cfg.rho_cut * c->cfg.rho_cut * sigma * sigma);
+        kc.w2_lo = (float)(c->leaf_w * c->leaf_w * (1.0 - 1e-4));
         kc.L = (float)c->cfg.box;
-        const int per_block = P3_THREADS * P3_TPT;
-        int chunks3 = (c->max_leaf + per_block - 1) / per_block;
+        int chunks3 = (c->max_leaf + P3_TARGETS - 1) / P3_TARGETS;
         if (chunks3 < 1) chunks3 = 1;
         if (chunks3 > 65535) chunks3 = 65535;
         dim3 grid3((unsigned)c->nleaf, (unsigned)chunks3);
