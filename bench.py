@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--k0", type=int, default=4)
     ap.add_argument("--m2l", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3"])
     ap.add_argument("--periodic-levels", type=int, default=2)
+    ap.add_argument("--depth", type=int, default=0, help="tree depth (0 = from the mean leaf occupancy)")
     ap.add_argument("--rho-cut", type=float, default=5.0,
                     help="pairs closer than rho_cut sigma take the smoothed kernel, farther ones the singular")
     ap.add_argument("--check", type=int, default=16, help="sampled targets for the oracle error (0 = off)")
@@ -340,7 +341,8 @@ def main():
     G = torch.tensor(f["alpha"], dtype=torch.float32, device=dev)
     U = torch.empty_like(G)
     S = torch.empty_like(G)
-    h = vf.VortexFMM(p=args.p, periodic_levels=args.periodic_levels, m2l=args.m2l, rho_cut=args.rho_cut)
+    h = vf.VortexFMM(p=args.p, periodic_levels=args.periodic_levels, m2l=args.m2l, rho_cut=args.rho_cut,
+                     depth=args.depth)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -410,7 +412,7 @@ def main():
         import oracle
         tid = wl.target_subset(N, args.check, seed=3)
         uo, so = oracle.direct(f["x"], f["alpha"], sigma, K=1, targets=tid)
-        h0 = vf.VortexFMM(p=args.p, periodic_levels=0, m2l=args.m2l, rho_cut=args.rho_cut)
+        h0 = vf.VortexFMM(p=args.p, periodic_levels=0, m2l=args.m2l, rho_cut=args.rho_cut, depth=args.depth)
         h0.build_tree(X)
         u0, s0 = h0.eval(G, sigma)
         h0.sync()

@@ -206,6 +206,15 @@ template <typename T> int build_operators(Ctx *c)
         kb.push_back(make_int4(g, 0, 0, 0));
     }
     if ((st = upload_vec(c, c->kblocks, kb, "k-block lists"))) return st;
+    std::vector<int4> cls;
+    for (int R = 1; R <= 2; ++R)
+        for (int g = 0; g < 8; ++g) {
+            c->cls_off[R][g] = (int)(cls.size() / 3);
+            build_line_classes(kb, c->kb_m2l_off[R][g], c->kb_m2l_cnt[R][g], g, cls);
+            c->cls_cnt[R][g] = (int)(cls.size() / 3) - c->cls_off[R][g];
+            if (c->cls_cnt[R][g] > 96) return fail(c, VFMM_ERR_UNSUPPORTED, "M2L offset classes exceed 96");
+        }
+    if ((st = upload_vec(c, c->cls, cls, "M2L offset classes"))) return st;
     return VFMM_OK;
 }
 
@@ -291,7 +300,7 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
             if (tc && l >= 3) {
                 bool bf = c->cfg.m2l_prec == VFMM_M2L_BF16X3;
                 if ((rc = launch_split(c, l, bf))) return rc;
-                if ((rc = launch_tc_m2l(c, l, kbd, c->kb_m2l_off[Rl], c->kb_m2l_cnt[Rl], bf))) return rc;
+                if ((rc = launch_tc_m2l(c, l, Rl, bf))) return rc;
                 continue;
             }
             GemmParams gp = {};
@@ -401,7 +410,8 @@ int build_impl(Ctx *c, int64_t n, const void *x, double sigma_hint = 0.0)
         if ((st = ensure(c, c->lexp, tot * esz, "locals"))) return st;
         if ((st = ensure(c, c->ufar, (size_t)n * 3 * esz, "far velocity"))) return st;
         if (c->cfg.m2l_prec == VFMM_M2L_TF32X3 || c->cfg.m2l_prec == VFMM_M2L_BF16X3) {
-            size_t cnt = ((size_t)1 << (3 * D)) * 3 * c->pc;
+            size_t cnt = 0;
+            for (int l = 3; l <= D; ++l) cnt = std::max(cnt, split_count(l, c->pc));
             size_t eb = c->cfg.m2l_prec == VFMM_M2L_BF16X3 ? 2 : 4;
             if ((st = ensure(c, c->mhi, cnt * eb, "multipole hi"))) return st;
             if ((st = ensure(c, c->mlo, cnt * eb, "multipole lo"))) return st;
@@ -509,7 +519,7 @@ int vfmm_destroy(vfmm_handle h)
     DevBuf *bufs[] = {&c->xs, &c->gs, &c->perm, &c->keys, &c->leaf_start, &c->counts, &c->fill, &c->tmpidx,
                       &c->scan_part, &c->err, &c->maxleaf, &c->bbox, &c->oct_start, &c->oct_box, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->ufar,
                       &c->sfar, &c->gfar, &c->adj_u, &c->adj_g1, &c->adj_g2, &c->rk_u1, &c->rk_s1, &c->rk_u2, &c->rk_s2, &c->rk_x1, &c->rk_g1, &c->diag, &c->rg_om, &c->rg_r, &c->rg_d, &c->rg_q, &c->rg_t1, &c->rg_t2, &c->rg_dots, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->m2m_f64,
-                      &c->lattice_f64, &c->root_m, &c->kblocks, &c->hx, &c->hg, &c->hu, &c->hs};
+                      &c->lattice_f64, &c->root_m, &c->kblocks, &c->cls, &c->hx, &c->hg, &c->hu, &c->hs};
     for (DevBuf *b : bufs) release(*b);
     if (c->have_events)
         for (int i = 0; i < 10; ++i) cudaEventDestroy(c->ev[i]);

@@ -30,7 +30,6 @@ constexpr int TC_CELLS = 64;
 constexpr int TC_N = 3 * TC_CELLS;          // 192 columns
 constexpr int TC_M = 128;
 constexpr int TC_STAGES = 5;                 // 5 x 20 KB: two CTAs (and two 256-column TMEM blocks) per SM
-constexpr int TC_PREFETCH = 3;               // stage i+3 refills the slot of MMA i-2
 constexpr int TC_A_BYTES = TC_M * TC_KBYTES;     // 4 KB
 constexpr int TC_B_BYTES = TC_N * TC_KBYTES;     // 6 KB
 constexpr int TC_STAGE_BYTES = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // 20 KB
@@ -43,14 +42,22 @@ constexpr long long TC_WAIT_LIMIT = 1LL << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+__device__ __forceinline__ float to_tf32_dev(float v)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout = 0)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
     d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-    // base offset 0, relative LBO, layout type 0 = no swizzle
+    // base offset 0, relative LBO; layout type (bits 61-63): 0 = no swizzle
+    d |= (uint64_t)(layout & 7u) << 61;
     return d;
 }
 
@@ -312,6 +319,258 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Source-line variant for levels with 16 to 64 cells per side and parity.
+//
+// The hi/lo multipoles of the level are first rearranged by parity into
+//   G[b][X][Y][Zp][component][coefficient],  b = parity (bx, by, bz), Zp = Z + 2 (two halo
+// cells on each side of every z-line, copied periodically).
+// A CTA owns whole z-lines of target cells of one parity g (128 cells: N = 384 columns of TMEM).
+// For an offset t the sources of a target line are one z-line of G (parity b = (g + t) mod 2,
+// line shifted by (g + t) >> 1 in x and y) read through a z window shifted by shz = (g_z + t_z) >> 1.
+// Offsets that share (b, shx, shy) form a class (up to three offsets, differing in shz): the
+// class's source lines are gathered into shared memory once per K slice, in the no-swizzle
+// K-major layout with 16-byte rows ([k-group][row][16 B]) and rows ordered (Zp, line,
+// component), so the window of every offset of the class is one contiguous run of 384 rows
+// starting 3 LINES (shz + 2) rows in: two MMAs (N = 192) per offset and split product.  Each
+// gathered source row serves all offsets of its class and each translation-matrix tile 384
+// columns.
+constexpr int TL_CELLS = 128;              // target cells per CTA (whole z-lines)
+constexpr int TL_N = 3 * TL_CELLS;         // accumulator columns
+constexpr int TL_HALO = 2;                 // |shz| <= 2
+constexpr int TL_MAXOFF = 3;               // offsets per class (the z parity leaves at most three)
+constexpr int TL_STAGES = 4;
+constexpr int TL_PF = 2;
+constexpr int TL_MAXCLS = 96;
+constexpr int TL_TMEM_COLS = 512;
+constexpr int TL_THREADS = 32 + TC_THREADS;  // MMA warp + 4 producer warps
+// shared bytes of one stage: up to four A tiles (hi, lo) and the class's source lines (hi, lo)
+template <int H> struct TlGeom {
+    static constexpr int LINES = TL_CELLS / H;
+    static constexpr int ROWS_LINE = (H + 2 * TL_HALO) * 3;  // rows of one source line in G
+    static constexpr int ROWS = (H + 2 * TL_HALO) * LINES * 3;  // staged rows (Zp, line, component)
+    static constexpr int ROW_Z = LINES * 3;                  // staged rows per z step
+    static constexpr int PLANE = ROWS * 16;                  // bytes of one 16-byte k-group plane
+    static constexpr int A_BYTES = TL_MAXOFF * 2 * TC_A_BYTES;
+    static constexpr int B_BYTES = 2 * TC_KG * PLANE;        // hi and lo
+    static constexpr int STAGE = (A_BYTES + B_BYTES + 1023) / 1024 * 1024;
+    static constexpr int SMEM = TL_STAGES * STAGE + 1024 + 256 + TL_MAXCLS * 48;
+    static constexpr int CHUNKS = ROWS * TC_KG;              // 16-byte copies per stage (each of hi, lo)
+    static_assert(TL_N == 2 * 192, "two MMAs of N = 192 per offset and product");
+    static_assert(SMEM <= 232448, "shared memory per CTA");
+};
+
+template <bool BF16, int H>
+__global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const int4 *__restrict__ cls, int ncls_g0)
+{
+    using Gm = TlGeom<H>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *stages = base;
+    uint64_t *full = (uint64_t *)(base + TL_STAGES * Gm::STAGE);
+    uint64_t *empty = full + TL_STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(empty + TL_STAGES);
+    int4 *cls_s = (int4 *)(base + TL_STAGES * Gm::STAGE + 256);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = blockIdx.y;
+    const int n = tp.n;
+    const int line0 = blockIdx.x * Gm::LINES;  // first target line (px * H + py) of this CTA
+    const int ncls = min(tp.kb_cnt[g], TL_MAXCLS);
+    for (int q = tid; q < 3 * ncls; q += TL_THREADS) cls_s[q] = cls[3 * tp.kb_off[g] + q];
+    (void)ncls_g0;
+    const int nchunk = tp.nchunk;
+    const int nk = ncls * nchunk;
+    const int pc = tp.pc;
+    const int esz = BF16 ? 2 : 4;
+
+    if (tid == 0) {
+        for (int s = 0; s < TL_STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), TC_THREADS / 32 + 1);  // one arrival per producer warp + expect_tx
+            mbar_init(smem_u32(&empty[s]), 1);                  // tcgen05.commit
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TL_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0) {
+        // ------------------------------- MMA issuer -------------------------------
+        if (tid == 0) {
+            const uint32_t fmt = BF16 ? 1u : 2u;
+            const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(192 >> 3) << 17) |
+                                   ((uint32_t)(TC_M >> 4) << 24);
+            for (int i = 0; i < nk; ++i) {
+                const int s = i % TL_STAGES;
+                if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((i / TL_STAGES) & 1))) {
+                    ok = false;
+                    break;
+                }
+                fence_proxy_async();  // producer cp.async writes (generic proxy) before the MMA reads
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const int ci = i / nchunk;
+                const int4 hd = cls_s[3 * ci], e01 = cls_s[3 * ci + 1], e23 = cls_s[3 * ci + 2];
+                const int cnt = min(hd.w, TL_MAXOFF);
+                const uint32_t st = smem_u32(stages + s * Gm::STAGE);
+                const uint32_t sB = st + Gm::A_BYTES, sBl = sB + TC_KG * Gm::PLANE;
+                for (int e = 0; e < cnt; ++e) {
+                    const int shz = e == 0 ? e01.y : e == 1 ? e01.w : e23.y;
+                    const uint32_t sA = st + (uint32_t)(e * 2 * TC_A_BYTES), sAl = sA + TC_A_BYTES;
+                    const uint64_t dAh = make_desc(sA, 128, TC_SBO), dAl = make_desc(sAl, 128, TC_SBO);
+                    const uint32_t acc0 = (i > 0 || e > 0) ? 1u : 0u;
+#pragma unroll
+                    for (int hfl = 0; hfl < 2; ++hfl) {
+                        const uint32_t woff = (uint32_t)(((shz + TL_HALO) * Gm::ROW_Z + 192 * hfl) * 16);
+                        const uint64_t dBh = make_desc(sB + woff, Gm::PLANE, 128);
+                        const uint64_t dBl = make_desc(sBl + woff, Gm::PLANE, 128);
+                        const uint32_t td = tmem + (uint32_t)(192 * hfl);
+                        mma_issue<BF16>(td, dAh, dBh, idesc, acc0);
+                        mma_issue<BF16>(td, dAh, dBl, idesc, 1u);
+                        mma_issue<BF16>(td, dAl, dBh, idesc, 1u);
+                    }
+                }
+                mma_commit(smem_u32(&empty[s]));
+            }
+        }
+    } else {
+        // ------------------------------- producers ---------------------------------
+        const int ptid = tid - 32;
+        const unsigned char *Ahi = (const unsigned char *)tp.Ahi, *Alo = (const unsigned char *)tp.Alo;
+        const unsigned char *Bhi = (const unsigned char *)tp.Bhi, *Blo = (const unsigned char *)tp.Blo;
+        const size_t row_bytes = (size_t)pc * esz;
+        for (int i = 0; i < nk + TL_PF; ++i) {
+            if (i < nk) {
+                const int s = i % TL_STAGES;
+                if (i >= TL_STAGES &&
+                    !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((i / TL_STAGES) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                const int ci = i / nchunk, ch = i - ci * nchunk;
+                const int4 hd = cls_s[3 * ci], e01 = cls_s[3 * ci + 1], e23 = cls_s[3 * ci + 2];
+                const int cnt = min(hd.w, TL_MAXOFF);
+                const uint32_t st = smem_u32(stages + s * Gm::STAGE);
+                if (ptid == 0) {
+                    const uint32_t fb = smem_u32(&full[s]);
+                    mbar_expect_tx(fb, (uint32_t)(cnt * 2 * TC_A_BYTES));
+                    for (int e = 0; e < cnt; ++e) {
+                        const int tile = e == 0 ? e01.x : e == 1 ? e01.z : e23.x;
+                        const uint32_t sA = st + (uint32_t)(e * 2 * TC_A_BYTES);
+                        bulk_g2s(sA, Ahi + ((size_t)tile * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
+                        bulk_g2s(sA + TC_A_BYTES, Alo + ((size_t)tile * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
+                    }
+                }
+                // the class's source lines: line l of this CTA is target line (px, py); its source
+                // is G[bpar][(px + shx) mod H][(py + shy) mod H][all Zp], staged as rows (Zp, l, comp)
+                const int bpar = hd.x, shx = hd.y, shy = hd.z;
+                const uint32_t sB = st + Gm::A_BYTES, sBl = sB + TC_KG * Gm::PLANE;
+                for (int v = ptid; v < Gm::CHUNKS; v += TC_THREADS) {
+                    const int kg = v % TC_KG;
+                    const int r = v / TC_KG;                    // staged row (Zp, l, comp)
+                    const int zp = r / Gm::ROW_Z, rl = r - zp * Gm::ROW_Z;
+                    const int l = rl / 3, comp = rl - 3 * l;
+                    const int L = line0 + l;
+                    const int px = L / H, py = L - (L / H) * H;
+                    const int X = (px + shx) & (H - 1), Y = (py + shy) & (H - 1);
+                    const size_t srow = (((size_t)bpar * H + X) * H + Y) * Gm::ROWS_LINE + zp * 3 + comp;
+                    const size_t off = srow * row_bytes + (size_t)ch * TC_KBYTES + 16 * kg;
+                    const uint32_t dst = (uint32_t)(kg * Gm::PLANE + r * 16);
+                    cp_async16(sB + dst, Bhi + off);
+                    cp_async16(sBl + dst, Blo + off);
+                }
+            }
+            cp_async_commit();
+            if (i >= TL_PF) {
+                cp_async_wait<TL_PF>();
+                fence_proxy_async();
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(smem_u32(&full[(i - TL_PF) % TL_STAGES]));
+            }
+        }
+        cp_async_wait<0>();
+    }
+    // epilogue: wait for the last MMAs (bounded), then warps 0..3 read TMEM lanes 32w..32w+31
+    if (ok && nk > 0 && warp < 4) {
+        int li = nk - 1;
+        ok = mbar_wait(smem_u32(&empty[li % TL_STAGES]), (uint32_t)((li / TL_STAGES) & 1));
+    }
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok && warp < 4) {
+        const int k = 32 * warp + (tid & 31);
+        float *C = tp.C;
+        const int gx = (g >> 2) & 1, gy = (g >> 1) & 1, gz = g & 1;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TL_N; c0 += 16) {
+            uint32_t r[16];
+            uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int col = c0 + e;  // (z, line, component)
+                const int pz = col / (Gm::LINES * 3), w = col - pz * Gm::LINES * 3;
+                const int l = w / 3, comp = w - 3 * l;
+                const int L = line0 + l;
+                const int px = L / H, py = L - (L / H) * H;
+                const int64_t cell = ((int64_t)(2 * px + gx) * n + (2 * py + gy)) * n + (2 * pz + gz);
+                C[(cell * 3 + comp) * pc + k] = __uint_as_float(r[e]);
+            }
+        }
+    } else if (!ok && tid == 0) {
+        atomicOr(tp.err, ERRBIT_TIMEOUT);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TL_TMEM_COLS));
+    }
+}
+
+// FP32 multipoles [cell][3][pc] of one level -> hi/lo parity grid G[b][X][Y][Zp][3][pc]
+// (h = n/2 cells per side and parity, Zp = Z + 2 with two periodic halo cells per side).
+template <typename TS>
+__global__ void k_split_grid(int n, int pc, const float *__restrict__ M, TS *__restrict__ hi, TS *__restrict__ lo)
+{
+    const int h = n >> 1, zp = h + 2 * TL_HALO;
+    const int64_t count = (int64_t)8 * h * h * zp * 3 * pc;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int64_t r = i;
+    const int k = (int)(r % pc); r /= pc;
+    const int comp = (int)(r % 3); r /= 3;
+    const int Zp = (int)(r % zp); r /= zp;
+    const int Y = (int)(r % h); r /= h;
+    const int X = (int)(r % h); r /= h;
+    const int b = (int)r;
+    const int Z = (Zp - TL_HALO + h) & (h - 1);
+    const int64_t cell = ((int64_t)(2 * X + ((b >> 2) & 1)) * n + (2 * Y + ((b >> 1) & 1))) * n + (2 * Z + (b & 1));
+    const float v = M[(cell * 3 + comp) * pc + k];
+    if constexpr (sizeof(TS) == 2) {
+        __nv_bfloat16 hv = __float2bfloat16_rn(v);
+        hi[i] = hv;
+        lo[i] = __float2bfloat16_rn(v - __bfloat162float(hv));
+    } else {
+        float hv = to_tf32_dev(v);
+        hi[i] = hv;
+        lo[i] = to_tf32_dev(v - hv);
+    }
+}
+
 // FP32 multipoles -> hi/lo split in BF16 or TF32 (the latter kept in FP32 containers).
 __global__ void k_split_bf16(int64_t count, const float *__restrict__ M, __nv_bfloat16 *__restrict__ hi,
                              __nv_bfloat16 *__restrict__ lo)
@@ -341,10 +600,35 @@ __global__ void k_split_tf32(int64_t count, const float *__restrict__ M, float *
     lo[i] = to_tf32(v - h);
 }
 
+bool grid_level(int level)
+{
+    const int h = (1 << level) / 2;
+    return h >= 16 && h <= 64;
+}
+
+size_t split_count(int level, int pc)
+{
+    const int64_t n = (int64_t)1 << level;
+    if (!grid_level(level)) return (size_t)(n * n * n * 3 * pc);
+    const int64_t h = n / 2;
+    return (size_t)(8 * h * h * (h + 2 * TL_HALO) * 3 * pc);
+}
+
 int launch_split(Ctx *c, int level, bool bf16)
 {
-    int64_t count = ((int64_t)1 << (3 * level)) * 3 * c->pc;
     const float *M = (const float *)c->mexp.p + c->lvl_off[level];
+    if (grid_level(level)) {
+        int64_t count = (int64_t)split_count(level, c->pc);
+        int nb = (int)((count + 255) / 256);
+        if (bf16)
+            k_split_grid<__nv_bfloat16><<<nb, 256, 0, c->stream>>>(1 << level, c->pc, M, (__nv_bfloat16 *)c->mhi.p,
+                                                                  (__nv_bfloat16 *)c->mlo.p);
+        else
+            k_split_grid<float><<<nb, 256, 0, c->stream>>>(1 << level, c->pc, M, (float *)c->mhi.p, (float *)c->mlo.p);
+        VFMM_CUDA_CHECK_LAUNCH(c);
+        return VFMM_OK;
+    }
+    int64_t count = ((int64_t)1 << (3 * level)) * 3 * c->pc;
     int nb = (int)((count + 255) / 256);
     if (bf16)
         k_split_bf16<<<nb, 256, 0, c->stream>>>(count, M, (__nv_bfloat16 *)c->mhi.p, (__nv_bfloat16 *)c->mlo.p);
@@ -354,18 +638,68 @@ int launch_split(Ctx *c, int level, bool bf16)
     return VFMM_OK;
 }
 
-int launch_tc_m2l(Ctx *c, int level, const int4 *kb_dev, const int *kb_off, const int *kb_cnt, bool bf16)
+void build_line_classes(const std::vector<int4> &kb, int off, int cnt, int g, std::vector<int4> &out)
 {
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[bf16 ? 1 : 0]) {
-        cudaError_t e = bf16 ? cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)
-                             : cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    // group the offsets of one parity's list by (source parity, x shift, y shift)
+    const int gx = (g >> 2) & 1, gy = (g >> 1) & 1, gz = g & 1;
+    std::vector<int4> hd, e01, e23;
+    for (int q = 0; q < cnt; ++q) {
+        const int4 t = kb[off + q];
+        const int sx = gx + t.y, sy = gy + t.z, sz = gz + t.w;
+        const int bpar = ((sx & 1) << 2) | ((sy & 1) << 1) | (sz & 1);
+        const int shx = sx >> 1, shy = sy >> 1, shz = sz >> 1;
+        size_t k = 0;
+        while (k < hd.size() && !(hd[k].x == bpar && hd[k].y == shx && hd[k].z == shy && hd[k].w < TL_MAXOFF)) ++k;
+        if (k == hd.size()) {
+            hd.push_back(make_int4(bpar, shx, shy, 0));
+            e01.push_back(make_int4(0, 0, 0, 0));
+            e23.push_back(make_int4(0, 0, 0, 0));
+        }
+        int e = hd[k].w++;
+        int4 &d = e < 2 ? e01[k] : e23[k];
+        if (e % 2 == 0) {
+            d.x = t.x;
+            d.y = shz;
+        } else {
+            d.z = t.x;
+            d.w = shz;
+        }
+    }
+    for (size_t k = 0; k < hd.size(); ++k) {
+        out.push_back(hd[k]);
+        out.push_back(e01[k]);
+        out.push_back(e23[k]);
+    }
+}
+
+namespace {
+template <bool BF16, int H> int launch_lines(Ctx *c, int level, int R, const TcParams &tp0)
+{
+    using Gm = TlGeom<H>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_m2l_lines<BF16, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
         if (e != cudaSuccess) {
             c->last_error = std::string("tensor-core M2L shared memory: ") + cudaGetErrorString(e);
             return VFMM_ERR_CUDA;
         }
-        attr_set[bf16 ? 1 : 0] = true;
+        attr = true;
     }
+    TcParams tp = tp0;
+    for (int g = 0; g < 8; ++g) {
+        tp.kb_off[g] = c->cls_off[R][g];
+        tp.kb_cnt[g] = c->cls_cnt[R][g];
+    }
+    const int lines = H * H;  // target z-lines per parity
+    dim3 grid((unsigned)(lines / Gm::LINES), 8);
+    k_m2l_lines<BF16, H><<<grid, TL_THREADS, Gm::SMEM, c->stream>>>(tp, (const int4 *)c->cls.p, 0);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+}  // namespace
+
+int launch_tc_m2l(Ctx *c, int level, int R, bool bf16)
+{
     const int n = 1 << level;
     const int64_t ncg = (int64_t)(n / 2) * (n / 2) * (n / 2);
     if (ncg % TC_CELLS != 0 || c->pc != TC_M) {
@@ -378,15 +712,31 @@ int launch_tc_m2l(Ctx *c, int level, const int4 *kb_dev, const int *kb_off, cons
     tp.Bhi = c->mhi.p;
     tp.Blo = c->mlo.p;
     tp.C = (float *)c->lexp.p + c->lvl_off[level];
-    tp.kb = kb_dev;
+    tp.kb = (const int4 *)c->kblocks.p;
     for (int g = 0; g < 8; ++g) {
-        tp.kb_off[g] = kb_off[g];
-        tp.kb_cnt[g] = kb_cnt[g];
+        tp.kb_off[g] = c->kb_m2l_off[R][g];
+        tp.kb_cnt[g] = c->kb_m2l_cnt[R][g];
     }
     tp.n = n;
     tp.pc = c->pc;
     tp.nchunk = c->pc * (bf16 ? 2 : 4) / TC_KBYTES;
     tp.err = (int *)c->err.p;
+    if (grid_level(level)) {
+        const int h = n / 2;
+        if (h == 16) return bf16 ? launch_lines<true, 16>(c, level, R, tp) : launch_lines<false, 16>(c, level, R, tp);
+        if (h == 32) return bf16 ? launch_lines<true, 32>(c, level, R, tp) : launch_lines<false, 32>(c, level, R, tp);
+        return bf16 ? launch_lines<true, 64>(c, level, R, tp) : launch_lines<false, 64>(c, level, R, tp);
+    }
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[bf16 ? 1 : 0]) {
+        cudaError_t e = bf16 ? cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)
+                             : cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        if (e != cudaSuccess) {
+            c->last_error = std::string("tensor-core M2L shared memory: ") + cudaGetErrorString(e);
+            return VFMM_ERR_CUDA;
+        }
+        attr_set[bf16 ? 1 : 0] = true;
+    }
     dim3 grid((unsigned)(ncg / TC_CELLS), 8);
     if (bf16)
         k_m2l_tc<true><<<grid, TC_WS_THREADS, TC_SMEM, c->stream>>>(tp);

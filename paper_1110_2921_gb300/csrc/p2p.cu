@@ -133,7 +133,20 @@ struct P3Const {
     float d2_cut;      // (rho_cut sigma)^2: beyond the near rings, octants closer than this are corrected
     float w2_lo;       // leaf width squared, less a rounding margin
     float L;
+    float as[5];       // A&S 7.1.26 coefficients a1..a5
 };
+
+#ifndef VFMM_P3_CPOLY
+#define VFMM_P3_CPOLY 1
+#endif
+// t P(t) of A&S 7.1.26: erfc(x) = t P(t) exp(-x^2), t = 1/(1 + p x)
+__device__ __forceinline__ float as_poly(const P3Const &k, float t)
+{
+    if (VFMM_P3_CPOLY)
+        return t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, k.as[4], k.as[3]), k.as[2]), k.as[1]), k.as[0]);
+    return t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                    0.254829592f);
+}
 
 struct Acc3 {
     float A0, A1, A2, U0, U1, U2, D0, D1, D2, E0, E1, E2;
@@ -151,8 +164,7 @@ __device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, fl
         float rinv = rsqrt_approx(r2);
         float r = r2 * rinv;
         float t = rcp_approx(fmaf(r, k.ct, 1.0f));
-        float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
-                              0.254829592f);
+        float poly = as_poly(k, t);
         float omq = e * fmaf(k.cq, r, poly);  // 1 - q(rho)
         float rinv2 = rinv * rinv;
         K = -omq * (rinv2 * rinv);
@@ -167,8 +179,7 @@ __device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, fl
         float rinv = rsqrt_approx(r2);
         float r = r2 * rinv;
         float t = rcp_approx(fmaf(r, k.ct, 1.0f));
-        float poly = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
-                              0.254829592f);
+        float poly = as_poly(k, t);
         float q = fmaf(-e, fmaf(k.cq, r, poly), 1.0f);
         float rinv2 = rinv * rinv;
         K = q * (rinv2 * rinv);
@@ -313,7 +324,15 @@ constexpr int P2P_BS = 64;
 constexpr float INV_4PI_F = 0.0795774715459476679f;
 constexpr double INV_4PI_D = 0.0795774715459476679;
 
-__global__ void __launch_bounds__(P3_THREADS) k_p2p_f32(const float4 *__restrict__ xs, const float4 *__restrict__ gs,
+#ifndef VFMM_P3_MINB
+#define VFMM_P3_MINB 32  // full occupancy: 32 one-warp blocks per SM (64 registers)
+#endif
+#if VFMM_P3_MINB > 0
+#define VFMM_P3_BOUNDS __launch_bounds__(P3_THREADS, VFMM_P3_MINB)
+#else
+#define VFMM_P3_BOUNDS __launch_bounds__(P3_THREADS)
+#endif
+__global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const float4 *__restrict__ gs,
                                                         const int *__restrict__ ls, const float4 *__restrict__ bbox,
                                                         const int *__restrict__ oct_start,
                                                         const float4 *__restrict__ oct_box, int nside, int log2n,
@@ -556,6 +575,11 @@ int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void
         kc.d2_singular = (float)(42.25 * sigma * sigma);   // (6.5 sigma)^2
         kc.d2_cut = (float)(c->cfg.rho_cut * c->cfg.rho_cut * sigma * sigma);
         kc.w2_lo = (float)(c->leaf_w * c->leaf_w * (1.0 - 1e-4));
+        kc.as[0] = 0.254829592f;
+        kc.as[1] = -0.284496736f;
+        kc.as[2] = 1.421413741f;
+        kc.as[3] = -1.453152027f;
+        kc.as[4] = 1.061405429f;
         kc.L = (float)c->cfg.box;
         int chunks3 = (c->max_leaf + P3_TARGETS - 1) / P3_TARGETS;
         if (chunks3 < 1) chunks3 = 1;

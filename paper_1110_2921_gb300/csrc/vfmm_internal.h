@@ -107,6 +107,8 @@ struct Ctx {
 
     // k-block lists (offsets into kblocks)
     int kb_m2l_off[3][8], kb_m2l_cnt[3][8];  // index = near rings R at that level (1 or 2)
+    DevBuf cls;                              // M2L offset classes of the source-line kernel
+    int cls_off[3][8], cls_cnt[3][8];        // in classes (three int4 each)
     int kb_m2m_off = 0, kb_l2l_off[8];
 
     cudaEvent_t ev[10];
@@ -130,8 +132,12 @@ int launch_adjoint_combine(Ctx *c, const void *G1, const void *w, const void *G2
 // direct_K >= 0: direct sum over every leaf of the (2K+1)^3 image boxes; -1: the FMM near field (R rings)
 int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void *sfar, void *u_out,
                void *s_out, int direct_K);
-int launch_tc_m2l(Ctx *c, int level, const int4 *kb_dev, const int *kb_off, const int *kb_cnt, bool bf16);
+int launch_tc_m2l(Ctx *c, int level, int R, bool bf16);  // R: near rings excluded at this level
+// classes of one parity's M2L list for the source-line kernel: per class three int4
+// {source parity, x shift, y shift, count}, {tile, z shift, tile, z shift} x 2
+void build_line_classes(const std::vector<int4> &kb, int off, int cnt, int g, std::vector<int4> &out);
 int launch_split(Ctx *c, int level, bool bf16);
+size_t split_count(int level, int pc);  // hi/lo elements launch_split writes for one level
 void set_constants(int p);
 int launch_axpy3(Ctx *c, int64_t n, const void *a, const void *b, const void *d, double coef, double wrap_L, void *out);
 int launch_diag(Ctx *c, int64_t n, const void *x, const void *g, const void *u, double *out_dev);

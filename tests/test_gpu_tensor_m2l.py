@@ -71,3 +71,30 @@ def test_m2l_precisions_against_fp64_fmm_same_lists(field32, near_rings):
         eu, es = rel_l2(u, u64), rel_l2(s, s64)
         print("R=%d %s: u %.3e S %.3e" % (near_rings, m2l, eu, es))
         assert eu < tol and es < tol
+
+
+@pytest.mark.parametrize("m2l", ["bf16x3", "tf32x3"])
+def test_line_levels_match_fp32_m2l_128cubed(m2l):
+    # depth 5: level 5 (16 cells per side and parity) runs the source-line kernel, levels 3-4 the
+    # gathered one; every particle's u and S against the FP32 CUDA-core M2L on the same tree
+    f = wl.make_vortex_lattice(128, 4, 1)
+    kw = dict(p=10, depth=5, periodic_levels=2)
+    u32, s32, _ = run_fmm(f["x"], f["alpha"], f["sigma"], m2l="fp32", **kw)
+    u, s, info = run_fmm(f["x"], f["alpha"], f["sigma"], m2l=m2l, **kw)
+    eu, es = rel_l2(u, u32), rel_l2(s, s32)
+    print(m2l, info, eu, es)
+    assert eu < 4e-5 and es < 4e-5
+
+
+def test_line_levels_deep_tree_match_fp32_m2l():
+    # 64^3 particles on a depth-7 tree: levels 5, 6, 7 (16, 32, 64 cells per side and parity)
+    # all take the source-line kernel; sparse leaves, one near ring, correction ring 2
+    f = wl.make_vortex_lattice(64, 8, 1)
+    kw = dict(p=10, depth=7, periodic_levels=1, rho_cut=2.0)
+    sig = 0.25 * f["sigma"]
+    u32, s32, _ = run_fmm(f["x"], f["alpha"], sig, m2l="fp32", **kw)
+    u, s, info = run_fmm(f["x"], f["alpha"], sig, m2l="bf16x3", **kw)
+    eu, es = rel_l2(u, u32), rel_l2(s, s32)
+    print(info, eu, es)
+    assert info["depth"] == 7
+    assert eu < 4e-5 and es < 4e-5
