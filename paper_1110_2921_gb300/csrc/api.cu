@@ -417,6 +417,7 @@ int build_impl(Ctx *c, int64_t n, const void *x, double sigma_hint = 0.0)
             if ((st = ensure(c, c->mlo, cnt * eb, "multipole lo"))) return st;
         }
         if ((st = ensure(c, c->sfar, (size_t)n * 3 * esz, "far stretching"))) return st;
+        if ((st = ensure(c, c->gemm_part, (size_t)4 << 20 << (esz == 8 ? 1 : 0) << 2, "split-k partials"))) return st;
     }
     c->launches = 0;
     cudaEventRecord(c->ev[0], c->stream);
@@ -517,7 +518,7 @@ int vfmm_destroy(vfmm_handle h)
     Ctx *c = &h->c;
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->xs, &c->gs, &c->perm, &c->keys, &c->leaf_start, &c->counts, &c->fill, &c->tmpidx,
-                      &c->scan_part, &c->err, &c->maxleaf, &c->bbox, &c->oct_start, &c->oct_box, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->ufar,
+                      &c->scan_part, &c->err, &c->maxleaf, &c->bbox, &c->oct_start, &c->oct_box, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->gemm_part, &c->ufar,
                       &c->sfar, &c->gfar, &c->adj_u, &c->adj_g1, &c->adj_g2, &c->rk_u1, &c->rk_s1, &c->rk_u2, &c->rk_s2, &c->rk_x1, &c->rk_g1, &c->diag, &c->rg_om, &c->rg_r, &c->rg_d, &c->rg_q, &c->rg_t1, &c->rg_t2, &c->rg_dots, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->m2m_f64,
                       &c->lattice_f64, &c->root_m, &c->kblocks, &c->cls, &c->hx, &c->hg, &c->hu, &c->hs};
     for (DevBuf *b : bufs) release(*b);

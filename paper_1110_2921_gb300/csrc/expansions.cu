@@ -7,6 +7,8 @@
 // (Eqs. stretchingfmm1-2).  Coefficients use the balanced packed layout documented in
 // operators.cpp; every cell's block is [3][pc] (pc = padded coefficient stride).
 #include "common.cuh"
+
+#include <algorithm>
 #include "vfmm_internal.h"
 
 namespace vfmm {
@@ -259,14 +261,23 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm(GemmParams gp, int64_t ncell_
     typedef GemmCfg<T> C;
     constexpr int BK = C::BK, VEC = C::VEC;
     typedef typename C::vec vec;
-    __shared__ __align__(16) T As[2][BK][GM];
-    __shared__ __align__(16) T Bs[2][BK][GN];
+    constexpr int EPI = sizeof(T) == 4 ? 48 : 24;  // columns per epilogue pass through shared memory
+    constexpr int MAIN_BYTES = (2 * BK * GM + 2 * BK * GN) * (int)sizeof(T);
+    constexpr int EPI_BYTES = EPI * (GM + 4) * (int)sizeof(T);
+    __shared__ __align__(16) unsigned char smem[MAIN_BYTES > EPI_BYTES ? MAIN_BYTES : EPI_BYTES];
+    T (*As)[BK][GM] = reinterpret_cast<T (*)[BK][GM]>(smem);
+    T (*Bs)[BK][GN] = reinterpret_cast<T (*)[BK][GN]>(smem + 2 * BK * GM * sizeof(T));
+    T (*Cs)[GM + 4] = reinterpret_cast<T (*)[GM + 4]>(smem);
     const int g = gp.grouped ? blockIdx.y : 0;
     const int tid = threadIdx.x;
     const int tm = tid >> 4, tn = tid & 15;
     const int64_t cell0 = (int64_t)blockIdx.x * GCELLS;
-    const int nkb = gp.kb_cnt[g];
-    const int4 *kbl = gp.kb + gp.kb_off[g];
+    // k-block slice of this block (split k over blockIdx.z)
+    const int nkb_all = gp.kb_cnt[g];
+    const int per = (nkb_all + gp.ksplit - 1) / gp.ksplit;
+    const int kb0 = min(nkb_all, (int)blockIdx.z * per);
+    const int nkb = min(nkb_all, kb0 + per) - kb0;
+    const int4 *kbl = gp.kb + gp.kb_off[g] + kb0;
     const int pc = gp.pc;
     const int nch = pc / BK;
     const int total = nkb * nch;
@@ -358,35 +369,97 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm(GemmParams gp, int64_t ncell_
         if (c + 1 < total) store(buf ^ 1);
         __syncthreads();
     }
-    // epilogue
-    T *Cp = (T *)gp.C;
+    // epilogue: the tile goes through shared memory so that every (cell, component) row of
+    // pc coefficients is written (or read-modify-written) by whole warps, vector by vector
+    const int64_t ntgt3 = (int64_t)gp.n_tgt * gp.n_tgt * gp.n_tgt;
+    T *Cp = gp.ksplit > 1 ? (T *)gp.partial + (int64_t)blockIdx.z * ntgt3 * 3 * pc : (T *)gp.C;
+    const bool acc_c = gp.accumulate && gp.ksplit == 1;
+    constexpr int RV = GM / VEC;  // vectors per row
+#pragma unroll 1
+    for (int c0 = 0; c0 < GN; c0 += EPI) {
+        __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        int n = tn * 6 + j;
-        int q = n / 3, comp = n - 3 * q;
-        int64_t cq = cell0 + q;
-        if (cq >= ncell_group) continue;
-        int cx, cy, cz;
-        target_cell(gp, g, cq, cx, cy, cz);
-        int64_t cell = ((int64_t)cx * gp.n_tgt + cy) * gp.n_tgt + cz;
-        T *row = Cp + (cell * 3 + comp) * pc;
+        for (int j = 0; j < 6; ++j) {
+            int n = tn * 6 + j - c0;
+            if (n >= 0 && n < EPI) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            int m = tm * 8 + i;
-            if (m < pc) row[m] = gp.accumulate ? row[m] + acc[i][j] : acc[i][j];
+                for (int i = 0; i < 8; ++i) Cs[n][tm * 8 + i] = acc[i][j];
+            }
+        }
+        __syncthreads();
+        for (int idx = tid; idx < EPI * RV; idx += GTHREADS) {
+            const int r = idx / RV, mv = idx - r * RV;
+            const int n = c0 + r;
+            const int q = n / 3, comp = n - 3 * q;
+            const int64_t cq = cell0 + q;
+            const int m = mv * VEC;
+            if (cq >= ncell_group || m >= pc) continue;
+            int cx, cy, cz;
+            target_cell(gp, g, cq, cx, cy, cz);
+            const int64_t cell = ((int64_t)cx * gp.n_tgt + cy) * gp.n_tgt + cz;
+            vec *dst = (vec *)(Cp + (cell * 3 + comp) * pc + m);
+            vec v = *(const vec *)&Cs[r][m];
+            if (acc_c) {
+                vec o = *dst;
+                T *pv = (T *)&v;
+                const T *po = (const T *)&o;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) pv[e] += po[e];
+            }
+            *dst = v;
         }
     }
 }
 
-int launch_gemm(Ctx *c, const GemmParams &gp, int ngroups, int64_t ncell_group)
+// Sum of the k slices in slice order (deterministic), into C (= or +=).
+template <typename T>
+__global__ void k_split_reduce(int nsplit, int64_t count, const T *__restrict__ partial, T *__restrict__ C,
+                               int accumulate)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    T s = accumulate ? C[i] : T(0);
+    for (int z = 0; z < nsplit; ++z) s += partial[(int64_t)z * count + i];
+    C[i] = s;
+}
+
+int launch_gemm(Ctx *c, const GemmParams &gp_in, int ngroups, int64_t ncell_group)
 {
     if (ncell_group <= 0) return VFMM_OK;
+    GemmParams gp = gp_in;
     dim3 grid((unsigned)((ncell_group + GCELLS - 1) / GCELLS), (unsigned)ngroups);
+    // small levels: split the k-block loop over more blocks (about four per SM), partial tiles
+    // summed by a second pass in a fixed order
+    int maxkb = 0;
+    for (int g = 0; g < ngroups; ++g) maxkb = std::max(maxkb, gp.kb_cnt[g]);
+    const int64_t blocks = (int64_t)grid.x * grid.y;
+    const int64_t ntgt3 = (int64_t)gp.n_tgt * gp.n_tgt * gp.n_tgt;
+    const int64_t count = ntgt3 * 3 * gp.pc;
+    int ksplit = 1;
+    if (blocks < 304 && maxkb > 1) {
+        ksplit = (int)std::min<int64_t>(maxkb, (608 + blocks - 1) / blocks);
+        const int64_t cap = (int64_t)(c->gemm_part.bytes / c->esz) / count;
+        ksplit = (int)std::min<int64_t>(ksplit, cap);
+        if (ksplit < 2) ksplit = 1;
+    }
+    gp.ksplit = ksplit;
+    gp.partial = c->gemm_part.p;
+    grid.z = (unsigned)ksplit;
     if (c->f64)
         k_gemm<double><<<grid, GTHREADS, 0, c->stream>>>(gp, ncell_group);
     else
         k_gemm<float><<<grid, GTHREADS, 0, c->stream>>>(gp, ncell_group);
     VFMM_CUDA_CHECK_LAUNCH(c);
+    if (ksplit > 1) {
+        const int nb = (int)((count + 255) / 256);
+        if (c->f64)
+            k_split_reduce<double><<<nb, 256, 0, c->stream>>>(ksplit, count, (const double *)gp.partial, (double *)gp.C,
+                                                              gp.accumulate);
+        else
+            k_split_reduce<float><<<nb, 256, 0, c->stream>>>(ksplit, count, (const float *)gp.partial, (float *)gp.C,
+                                                             gp.accumulate);
+        VFMM_CUDA_CHECK_LAUNCH(c);
+    }
     return VFMM_OK;
 }
 

@@ -17,17 +17,23 @@ __global__ void k_keys(int64_t n, const TIn *__restrict__ x, int nside, double L
                        int *__restrict__ counts)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double invL = 1.0 / L;
-    int c[3];
-    for (int d = 0; d < 3; ++d) {
-        double v = wrap_coord<double>((double)x[3 * i + d], L, invL);
-        int ci = (int)(v * invL * nside);
-        c[d] = ci < 0 ? 0 : (ci >= nside ? nside - 1 : ci);
+    const bool active = i < n;
+    int key = -1;
+    if (active) {
+        // coordinates in the input's own precision (FP64 arithmetic is scarce on this part)
+        const TIn Lt = (TIn)L, invL = (TIn)(1.0 / L), scale = (TIn)((double)nside / L);
+        int c[3];
+        for (int d = 0; d < 3; ++d) {
+            TIn v = wrap_coord<TIn>(x[3 * i + d], Lt, invL);
+            int ci = (int)(v * scale);
+            c[d] = ci < 0 ? 0 : (ci >= nside ? nside - 1 : ci);
+        }
+        key = (c[0] * nside + c[1]) * nside + c[2];
+        keys[i] = key;
     }
-    int key = (c[0] * nside + c[1]) * nside + c[2];
-    keys[i] = key;
-    atomicAdd(&counts[key], 1);
+    // one atomic per distinct leaf in the warp (neighbouring particles share leaves)
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (active && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
 }
 
 // Exclusive scan, level 1: each block scans 1024 counts, writes local prefix and its total.

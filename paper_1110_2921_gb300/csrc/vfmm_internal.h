@@ -54,6 +54,8 @@ struct GemmParams {
     int grouped;      // 1: targets split by parity (grid.y = 8); 0: all cells
     int accumulate;   // C += instead of C =
     int pc;           // padded coefficient stride (multiple of 16)
+    int ksplit;       // k-block slices summed by a second pass (1 = none); set by launch_gemm
+    void *partial;    // [ksplit][n_tgt^3][3][pc] slice results when ksplit > 1
 };
 
 struct TcParams {
@@ -91,6 +93,7 @@ struct Ctx {
     DevBuf oct_start, oct_box;     // per leaf: 8 octant starts (relative), 8 x (lo, hi) octant boxes
     DevBuf mexp, lexp;             // all levels, T
     DevBuf mhi, mlo;               // tensor-core copies of the multipoles (largest level)
+    DevBuf gemm_part;              // split-k partial results of the CUDA-core GEMM (small levels)
     DevBuf ufar, sfar, gfar;       // far-field u, S (or grad u) in sorted order, T
     DevBuf adj_u, adj_g1, adj_g2;  // adjoint temporaries (caller order)
     DevBuf rk_u1, rk_s1, rk_u2, rk_s2, rk_x1, rk_g1;  // time-step temporaries (caller order)
