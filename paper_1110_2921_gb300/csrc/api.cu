@@ -417,7 +417,7 @@ int build_impl(Ctx *c, int64_t n, const void *x, double sigma_hint = 0.0)
             if ((st = ensure(c, c->mlo, cnt * eb, "multipole lo"))) return st;
         }
         if ((st = ensure(c, c->sfar, (size_t)n * 3 * esz, "far stretching"))) return st;
-        if ((st = ensure(c, c->gemm_part, (size_t)4 << 20 << (esz == 8 ? 1 : 0) << 2, "split-k partials"))) return st;
+        if ((st = ensure(c, c->gemm_part, (size_t)64 << 20, "split-k partials"))) return st;
     }
     c->launches = 0;
     cudaEventRecord(c->ev[0], c->stream);

@@ -450,16 +450,19 @@ int launch_gemm(Ctx *c, const GemmParams &gp_in, int ngroups, int64_t ncell_grou
     else
         k_gemm<float><<<grid, GTHREADS, 0, c->stream>>>(gp, ncell_group);
     VFMM_CUDA_CHECK_LAUNCH(c);
-    if (ksplit > 1) {
-        const int nb = (int)((count + 255) / 256);
-        if (c->f64)
-            k_split_reduce<double><<<nb, 256, 0, c->stream>>>(ksplit, count, (const double *)gp.partial, (double *)gp.C,
-                                                              gp.accumulate);
-        else
-            k_split_reduce<float><<<nb, 256, 0, c->stream>>>(ksplit, count, (const float *)gp.partial, (float *)gp.C,
-                                                             gp.accumulate);
-        VFMM_CUDA_CHECK_LAUNCH(c);
-    }
+    if (ksplit > 1) return launch_split_reduce(c, ksplit, count, gp.partial, gp.C, gp.accumulate, !c->f64);
+    return VFMM_OK;
+}
+
+int launch_split_reduce(Ctx *c, int nsplit, int64_t count, const void *partial, void *C, int accumulate, bool f32)
+{
+    const int nb = (int)((count + 255) / 256);
+    if (f32)
+        k_split_reduce<float><<<nb, 256, 0, c->stream>>>(nsplit, count, (const float *)partial, (float *)C, accumulate);
+    else
+        k_split_reduce<double><<<nb, 256, 0, c->stream>>>(nsplit, count, (const double *)partial, (double *)C,
+                                                          accumulate);
+    VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
 }
 
@@ -587,12 +590,17 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
                                                 const T *__restrict__ Lc, T *__restrict__ ufar, T *__restrict__ sfar,
                                                 T *__restrict__ gfar)
 {
+    // Per leaf, the local expansion of psi is turned into the tables of the velocity
+    //   U_a = eps_abc D^b Psi_c            (degrees < p)
+    // and of its gradient D^k U_a (degrees < p - 1); each particle then sums conj(Y) T over
+    // the 3 + 9 tables: u_a, and du_a/dx_k, which gives S = (gamma . grad) u and, for the
+    // adjoint, the velocity gradient itself.
     typedef typename C2<T>::type T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ncx = (p + 1) * (p + 2) / 2;
-    T2 *F = (T2 *)smem_raw;    // [3][ncx]       local coefficients times s_nm
-    T2 *G = F + 3 * ncx;       // [3 dir][3 comp][ncx]   d_dir psi_comp (degrees < p)
-    T2 *H = G + 9 * ncx;       // [6 pair][3 comp][ncx]  d_a d_b psi_comp (degrees < p - 1)
+    T2 *F = (T2 *)smem_raw;    // [3][ncx]  local coefficients times s_nm
+    T2 *U = F + 3 * ncx;       // [3][ncx]  velocity tables
+    T2 *W = U + 3 * ncx;       // [ncx][12] per coefficient: U_0..2, then D^k U_a at 3 + 3k + a
     const int leaf = blockIdx.x;
     const int b0 = ls[leaf], e0 = ls[leaf + 1];
     if (e0 <= b0) return;
@@ -609,18 +617,23 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
     }
     __syncthreads();
     const int ng = p * (p + 1) / 2;  // entries of degree < p
-    for (int it = threadIdx.x; it < 9 * ng; it += blockDim.x) {
-        int ci = it % ng, rest = it / ng;
-        int comp = rest % 3, dir = rest / 3;
-        G[(dir * 3 + comp) * ncx + ci] = dcx<T>(F + comp * ncx, p, dir, c_cn[ci], c_cm[ci]);
+    for (int it = threadIdx.x; it < 3 * ng; it += blockDim.x) {
+        int ci = it % ng, a = it / ng;
+        int b = a == 2 ? 0 : a + 1, c = a == 0 ? 2 : a - 1;
+        T2 x1 = dcx<T>(F + c * ncx, p, b, c_cn[ci], c_cm[ci]);
+        T2 x2 = dcx<T>(F + b * ncx, p, c, c_cn[ci], c_cm[ci]);
+        T2 v;
+        v.x = x1.x - x2.x;
+        v.y = x1.y - x2.y;
+        U[a * ncx + ci] = v;
+        W[ci * 12 + a] = v;
     }
     __syncthreads();
     const int nh = (p - 1) * p / 2;  // entries of degree < p - 1
-    const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
-    for (int it = threadIdx.x; it < 18 * nh; it += blockDim.x) {
+    for (int it = threadIdx.x; it < 9 * nh; it += blockDim.x) {
         int ci = it % nh, rest = it / nh;
-        int comp = rest % 3, pr = rest / 3;
-        H[(pr * 3 + comp) * ncx + ci] = dcx<T>(G + (pa[pr] * 3 + comp) * ncx, p - 1, pb[pr], c_cn[ci], c_cm[ci]);
+        int a = rest % 3, k = rest / 3;
+        W[ci * 12 + 3 + 3 * k + a] = dcx<T>(U + a * ncx, p - 1, k, c_cn[ci], c_cm[ci]);
     }
     __syncthreads();
     const T zx = (cx + T(0.5)) * w, zy = (cy + T(0.5)) * w, zz = (cz + T(0.5)) * w;
@@ -629,9 +642,9 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
         typename V4<T>::type xp = xs[i];
         T x = (xp.x - zx) * invw, y = (xp.y - zy) * invw, z = (xp.z - zz) * invw;
         T r2 = x * x + y * y + z * z;
-        T A[27];
+        T A[12];
 #pragma unroll
-        for (int v = 0; v < 27; ++v) A[v] = 0;
+        for (int v = 0; v < 12; ++v) A[v] = 0;
         T dre = 1, dim = 0;
         for (int m = 0; m < p; ++m) {
             if (m > 0) {
@@ -658,17 +671,32 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
                     pre = cre;
                     pim = cim;
                 }
-                T wre = wgt * cre, wim = wgt * cim;
+                const T wre = wgt * cre, wim = wgt * cim;
+                const T2 *row = W + ci * 12;
+                if constexpr (sizeof(T) == 4) {
+                    // rows are 96 B and W starts 48 ncx bytes in: 16-byte loads of two entries
+                    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+                    const int nv = n < p - 1 ? 6 : 1;
 #pragma unroll
-                for (int v = 0; v < 9; ++v) {
-                    T2 t = G[v * ncx + ci];
-                    A[v] += wre * t.x + wim * t.y;
-                }
-                if (n < p - 1) {
+                    for (int v2 = 0; v2 < 6; ++v2) {
+                        if (v2 < nv) {
+                            float4 q = r4[v2];
+                            A[2 * v2] += wre * q.x + wim * q.y;
+                            A[2 * v2 + 1] += wre * q.z + wim * q.w;
+                        }
+                    }
+                    if (nv == 1) {
+                        T2 t = row[2];
+                        A[2] += wre * t.x + wim * t.y;
+                    }
+                } else {
+                    const int nv = n < p - 1 ? 12 : 3;
 #pragma unroll
-                    for (int v = 0; v < 18; ++v) {
-                        T2 t = H[v * ncx + ci];
-                        A[9 + v] += wre * t.x + wim * t.y;
+                    for (int v = 0; v < 12; ++v) {
+                        if (v < nv) {
+                            T2 t = row[v];
+                            A[v] += wre * t.x + wim * t.y;
+                        }
                     }
                 }
                 ci += n + 1;
@@ -677,37 +705,20 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
         // psi_c = (1/4pi)(1/w) sum conj(Y) s F; d/dx = (1/w) d/dy
         const T s1 = T(0.0795774715459476679) * invw * invw;
         const T s2 = s1 * invw;
-        // A[dir*3 + comp] = d_dir psi_comp ; A[9 + pair*3 + comp] with pairs xx xy xz yy yz zz
-        auto gr = [&](int comp, int dir) -> T { return A[dir * 3 + comp]; };
-        auto Hc = [&](int comp, int kk, int bb) -> T {
-            int lo = kk < bb ? kk : bb, hi = kk < bb ? bb : kk;
-            int idx = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
-            return A[9 + idx * 3 + comp];
-        };
-        ufar[3 * (int64_t)i + 0] = s1 * (gr(2, 1) - gr(1, 2));
-        ufar[3 * (int64_t)i + 1] = s1 * (gr(0, 2) - gr(2, 0));
-        ufar[3 * (int64_t)i + 2] = s1 * (gr(1, 0) - gr(0, 1));
-        if (sfar) {
+        ufar[3 * (int64_t)i + 0] = s1 * A[0];
+        ufar[3 * (int64_t)i + 1] = s1 * A[1];
+        ufar[3 * (int64_t)i + 2] = s1 * A[2];
+        if (sfar) {  // S_a = gamma_k du_a/dx_k
             typename V4<T>::type gp = gs[i];
-            T gk[3] = {gp.x, gp.y, gp.z};
-            T S0 = 0, S1 = 0, S2 = 0;
-#pragma unroll
-            for (int kk = 0; kk < 3; ++kk) {
-                S0 += gk[kk] * (Hc(2, kk, 1) - Hc(1, kk, 2));
-                S1 += gk[kk] * (Hc(0, kk, 2) - Hc(2, kk, 0));
-                S2 += gk[kk] * (Hc(1, kk, 0) - Hc(0, kk, 1));
-            }
-            sfar[3 * (int64_t)i + 0] = s2 * S0;
-            sfar[3 * (int64_t)i + 1] = s2 * S1;
-            sfar[3 * (int64_t)i + 2] = s2 * S2;
+            sfar[3 * (int64_t)i + 0] = s2 * (gp.x * A[3] + gp.y * A[6] + gp.z * A[9]);
+            sfar[3 * (int64_t)i + 1] = s2 * (gp.x * A[4] + gp.y * A[7] + gp.z * A[10]);
+            sfar[3 * (int64_t)i + 2] = s2 * (gp.x * A[5] + gp.y * A[8] + gp.z * A[11]);
         }
-        if (gfar) {  // velocity gradient du_a/dx_k = eps_abc d_k d_b psi_c
+        if (gfar) {  // velocity gradient du_a/dx_k at 3a + k
 #pragma unroll
-            for (int kk = 0; kk < 3; ++kk) {
-                gfar[9 * (int64_t)i + 0 + kk] = s2 * (Hc(2, kk, 1) - Hc(1, kk, 2));
-                gfar[9 * (int64_t)i + 3 + kk] = s2 * (Hc(0, kk, 2) - Hc(2, kk, 0));
-                gfar[9 * (int64_t)i + 6 + kk] = s2 * (Hc(1, kk, 0) - Hc(0, kk, 1));
-            }
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk) gfar[9 * (int64_t)i + 3 * a + kk] = s2 * A[3 + 3 * kk + a];
         }
     }
 }
@@ -718,7 +729,7 @@ int launch_l2p(Ctx *c, bool grad)
     while ((1 << log2n) < c->nside) ++log2n;
     size_t off = c->lvl_off[c->depth];
     const int ncx = (c->p + 1) * (c->p + 2) / 2;
-    size_t sm = (size_t)(3 + 9 + 18) * ncx * 2 * c->esz;
+    size_t sm = (size_t)(3 + 3 + 12) * ncx * 2 * c->esz;
     if (c->f64)
         k_l2p<double><<<(unsigned)c->nleaf, L2P_BS, sm, c->stream>>>(
             (const dvec4 *)c->xs.p, (const dvec4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,

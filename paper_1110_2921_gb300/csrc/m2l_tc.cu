@@ -23,6 +23,8 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 namespace vfmm {
 
 constexpr int TC_THREADS = 128;
@@ -158,8 +160,12 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
     const int g = blockIdx.y;
     const int n = tp.n, half = n >> 1;
     const int64_t cell0 = (int64_t)blockIdx.x * TC_CELLS;
-    const int nkb = min(tp.kb_cnt[g], TC_MAXKB);
-    for (int q = tid; q < nkb; q += TC_WS_THREADS) kb_s[q] = tp.kb[tp.kb_off[g] + q];
+    // k-block slice of this CTA (small levels split the offsets over blockIdx.z)
+    const int nkb_all = min(tp.kb_cnt[g], TC_MAXKB);
+    const int per = (nkb_all + tp.ksplit - 1) / tp.ksplit;
+    const int kb0 = min(nkb_all, (int)blockIdx.z * per);
+    const int nkb = min(nkb_all, kb0 + per) - kb0;
+    for (int q = tid; q < nkb; q += TC_WS_THREADS) kb_s[q] = tp.kb[tp.kb_off[g] + kb0 + q];
     for (int q = tid; q < TC_CELLS; q += TC_WS_THREADS) {
         int64_t P = cell0 + q;
         int px = (int)(P / ((int64_t)half * half)), py = (int)((P / half) % half), pz = (int)(P % half);
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok && warp < 4) {
         const int k = 32 * warp + (tid & 31);
-        float *C = tp.C;
+        float *C = tp.ksplit > 1 ? tp.partial + (int64_t)blockIdx.z * tp.n * tp.n * tp.n * 3 * pc : tp.C;
 #pragma unroll 1
         for (int c0 = 0; c0 < TC_N; c0 += 16) {
             uint32_t r[16];
@@ -322,9 +328,12 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
 // ---------------------------------------------------------------------------------------
 // Source-line variant for levels with 16 to 64 cells per side and parity.
 //
-// The hi/lo multipoles of the level are first rearranged by parity into
-//   G[b][X][Y][Zp][component][coefficient],  b = parity (bx, by, bz), Zp = Z + 2 (two halo
-// cells on each side of every z-line, copied periodically).
+// The hi/lo multipoles of the level are first rearranged by K slice and parity into
+//   G[slice][b][X][Y][Zp][component][32 bytes of coefficients],  b = parity (bx, by, bz),
+//   Zp = Z + 2 (two halo cells on each side of every z-line, copied periodically),
+// so that one K slice of a source line is one contiguous run of rows.  The CTA walks the K
+// slices in the outer loop: the CTAs resident at one time then share the slice's source lines
+// in L2.
 // A CTA owns whole z-lines of target cells of one parity g (128 cells: N = 384 columns of TMEM).
 // For an offset t the sources of a target line are one z-line of G (parity b = (g + t) mod 2,
 // line shifted by (g + t) >> 1 in x and y) read through a z window shifted by shz = (g_z + t_z) >> 1.
@@ -382,7 +391,6 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
     const int nchunk = tp.nchunk;
     const int nk = ncls * nchunk;
     const int pc = tp.pc;
-    const int esz = BF16 ? 2 : 4;
 
     if (tid == 0) {
         for (int s = 0; s < TL_STAGES; ++s) {
@@ -417,7 +425,7 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
                 }
                 fence_proxy_async();  // producer cp.async writes (generic proxy) before the MMA reads
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const int ci = i / nchunk;
+                const int ci = i % ncls;
                 const int4 hd = cls_s[3 * ci], e01 = cls_s[3 * ci + 1], e23 = cls_s[3 * ci + 2];
                 const int cnt = min(hd.w, TL_MAXOFF);
                 const uint32_t st = smem_u32(stages + s * Gm::STAGE);
@@ -446,7 +454,6 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
         const int ptid = tid - 32;
         const unsigned char *Ahi = (const unsigned char *)tp.Ahi, *Alo = (const unsigned char *)tp.Alo;
         const unsigned char *Bhi = (const unsigned char *)tp.Bhi, *Blo = (const unsigned char *)tp.Blo;
-        const size_t row_bytes = (size_t)pc * esz;
         for (int i = 0; i < nk + TL_PF; ++i) {
             if (i < nk) {
                 const int s = i % TL_STAGES;
@@ -455,7 +462,7 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
                     ok = false;
                     break;
                 }
-                const int ci = i / nchunk, ch = i - ci * nchunk;
+                const int ch = i / ncls, ci = i - ch * ncls;
                 const int4 hd = cls_s[3 * ci], e01 = cls_s[3 * ci + 1], e23 = cls_s[3 * ci + 2];
                 const int cnt = min(hd.w, TL_MAXOFF);
                 const uint32_t st = smem_u32(stages + s * Gm::STAGE);
@@ -481,8 +488,8 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
                     const int L = line0 + l;
                     const int px = L / H, py = L - (L / H) * H;
                     const int X = (px + shx) & (H - 1), Y = (py + shy) & (H - 1);
-                    const size_t srow = (((size_t)bpar * H + X) * H + Y) * Gm::ROWS_LINE + zp * 3 + comp;
-                    const size_t off = srow * row_bytes + (size_t)ch * TC_KBYTES + 16 * kg;
+                    const size_t srow = (((size_t)(ch * 8 + bpar) * H + X) * H + Y) * Gm::ROWS_LINE + zp * 3 + comp;
+                    const size_t off = srow * TC_KBYTES + 16 * kg;
                     const uint32_t dst = (uint32_t)(kg * Gm::PLANE + r * 16);
                     cp_async16(sB + dst, Bhi + off);
                     cp_async16(sBl + dst, Blo + off);
@@ -543,15 +550,16 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
 
 // FP32 multipoles [cell][3][pc] of one level -> hi/lo parity grid G[b][X][Y][Zp][3][pc]
 // (h = n/2 cells per side and parity, Zp = Z + 2 with two periodic halo cells per side).
+// One thread per 8 consecutive coefficients (pc is a multiple of 8).
 template <typename TS>
 __global__ void k_split_grid(int n, int pc, const float *__restrict__ M, TS *__restrict__ hi, TS *__restrict__ lo)
 {
-    const int h = n >> 1, zp = h + 2 * TL_HALO;
-    const int64_t count = (int64_t)8 * h * h * zp * 3 * pc;
+    const int h = n >> 1, zp = h + 2 * TL_HALO, pv = pc >> 3;
+    const int64_t count = (int64_t)8 * h * h * zp * 3 * pv;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     int64_t r = i;
-    const int k = (int)(r % pc); r /= pc;
+    const int kv = (int)(r % pv); r /= pv;
     const int comp = (int)(r % 3); r /= 3;
     const int Zp = (int)(r % zp); r /= zp;
     const int Y = (int)(r % h); r /= h;
@@ -559,15 +567,36 @@ __global__ void k_split_grid(int n, int pc, const float *__restrict__ M, TS *__r
     const int b = (int)r;
     const int Z = (Zp - TL_HALO + h) & (h - 1);
     const int64_t cell = ((int64_t)(2 * X + ((b >> 2) & 1)) * n + (2 * Y + ((b >> 1) & 1))) * n + (2 * Z + (b & 1));
-    const float v = M[(cell * 3 + comp) * pc + k];
+    const float4 *src = (const float4 *)(M + (cell * 3 + comp) * pc + 8 * kv);
+    // destination: K slice of 32 bytes (16 BF16 / 8 TF32 coefficients) outermost
+    constexpr int VPS = TC_KBYTES / (8 * (int)sizeof(TS));  // 8-coefficient vectors per slice
+    const int ch = kv / VPS, part = kv - ch * VPS;
+    const int64_t srow = i / pv;  // (b, X, Y, Zp, comp)
+    const int64_t nrows = count / pv;
+    const int64_t o = ((int64_t)ch * nrows + srow) * VPS + part;  // in 8-coefficient vectors
+    const float4 a = src[0], c = src[1];
+    const float v[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
     if constexpr (sizeof(TS) == 2) {
-        __nv_bfloat16 hv = __float2bfloat16_rn(v);
-        hi[i] = hv;
-        lo[i] = __float2bfloat16_rn(v - __bfloat162float(hv));
+        __align__(16) __nv_bfloat16 hv[8], lv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            hv[e] = __float2bfloat16_rn(v[e]);
+            lv[e] = __float2bfloat16_rn(v[e] - __bfloat162float(hv[e]));
+        }
+        reinterpret_cast<uint4 *>(hi)[o] = *reinterpret_cast<const uint4 *>(hv);
+        reinterpret_cast<uint4 *>(lo)[o] = *reinterpret_cast<const uint4 *>(lv);
     } else {
-        float hv = to_tf32_dev(v);
-        hi[i] = hv;
-        lo[i] = to_tf32_dev(v - hv);
+        float hv[8], lv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            hv[e] = to_tf32_dev(v[e]);
+            lv[e] = to_tf32_dev(v[e] - hv[e]);
+        }
+        float4 *H = reinterpret_cast<float4 *>(hi) + 2 * o, *Lo = reinterpret_cast<float4 *>(lo) + 2 * o;
+        H[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        H[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+        Lo[0] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        Lo[1] = make_float4(lv[4], lv[5], lv[6], lv[7]);
     }
 }
 
@@ -618,7 +647,7 @@ int launch_split(Ctx *c, int level, bool bf16)
 {
     const float *M = (const float *)c->mexp.p + c->lvl_off[level];
     if (grid_level(level)) {
-        int64_t count = (int64_t)split_count(level, c->pc);
+        int64_t count = (int64_t)split_count(level, c->pc) / 8;  // 8 coefficients per thread
         int nb = (int)((count + 255) / 256);
         if (bf16)
             k_split_grid<__nv_bfloat16><<<nb, 256, 0, c->stream>>>(1 << level, c->pc, M, (__nv_bfloat16 *)c->mhi.p,
@@ -707,6 +736,8 @@ int launch_tc_m2l(Ctx *c, int level, int R, bool bf16)
         return VFMM_ERR_UNSUPPORTED;
     }
     TcParams tp;
+    tp.ksplit = 1;
+    tp.partial = nullptr;
     tp.Ahi = c->tc_hi.p;
     tp.Alo = c->tc_lo.p;
     tp.Bhi = c->mhi.p;
@@ -737,12 +768,35 @@ int launch_tc_m2l(Ctx *c, int level, int R, bool bf16)
         }
         attr_set[bf16 ? 1 : 0] = true;
     }
+    // few CTAs (levels 3 and 4): split the offsets over about two CTAs per SM, partial tiles
+    // summed by a second pass in a fixed order
     dim3 grid((unsigned)(ncg / TC_CELLS), 8);
+    const int64_t blocks = (int64_t)grid.x * grid.y;
+    const int64_t count = (int64_t)n * n * n * 3 * c->pc;
+    int maxkb = 0;
+    for (int g = 0; g < 8; ++g) maxkb = std::max(maxkb, tp.kb_cnt[g]);
+    int ksplit = 1;
+    if (blocks < 304) {
+        ksplit = (int)std::min<int64_t>(maxkb, (304 + blocks - 1) / blocks);
+        ksplit = (int)std::min<int64_t>(ksplit, (int64_t)(c->gemm_part.bytes / sizeof(float)) / count);
+        // every slice keeps at least one offset
+        while (ksplit > 1 && (int64_t)((maxkb + ksplit - 1) / ksplit) * (ksplit - 1) >= maxkb) --ksplit;
+        for (int g = 0; g < 8; ++g)
+            while (ksplit > 1 && (int64_t)((tp.kb_cnt[g] + ksplit - 1) / ksplit) * (ksplit - 1) >= tp.kb_cnt[g]) --ksplit;
+        if (ksplit < 1) ksplit = 1;
+    }
+    tp.ksplit = ksplit;
+    tp.partial = (float *)c->gemm_part.p;
+    grid.z = (unsigned)ksplit;
     if (bf16)
         k_m2l_tc<true><<<grid, TC_WS_THREADS, TC_SMEM, c->stream>>>(tp);
     else
         k_m2l_tc<false><<<grid, TC_WS_THREADS, TC_SMEM, c->stream>>>(tp);
     VFMM_CUDA_CHECK_LAUNCH(c);
+    if (ksplit > 1) {
+        int rc = launch_split_reduce(c, ksplit, count, tp.partial, tp.C, 0, true);
+        if (rc) return rc;
+    }
     return VFMM_OK;
 }
 

@@ -68,6 +68,8 @@ struct TcParams {
     int pc;                 // padded coefficient stride
     int nchunk;             // K chunks per matrix
     int *err;               // device error word
+    int ksplit;             // offset slices (blockIdx.z) summed by a second pass (1 = none)
+    float *partial;         // [ksplit][n^3][3][pc] slice results when ksplit > 1
 };
 
 struct Ctx {
@@ -140,6 +142,8 @@ int launch_tc_m2l(Ctx *c, int level, int R, bool bf16);  // R: near rings exclud
 // {source parity, x shift, y shift, count}, {tile, z shift, tile, z shift} x 2
 void build_line_classes(const std::vector<int4> &kb, int off, int cnt, int g, std::vector<int4> &out);
 int launch_split(Ctx *c, int level, bool bf16);
+// C (= or +=) sum over z < nsplit of partial[z][i], i < count, in z order (FP32 or FP64 by c->f64 unless forced)
+int launch_split_reduce(Ctx *c, int nsplit, int64_t count, const void *partial, void *C, int accumulate, bool f32);
 size_t split_count(int level, int pc);  // hi/lo elements launch_split writes for one level
 void set_constants(int p);
 int launch_axpy3(Ctx *c, int64_t n, const void *a, const void *b, const void *d, double coef, double wrap_L, void *out);
