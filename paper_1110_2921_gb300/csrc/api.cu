@@ -421,8 +421,8 @@ int build_impl(Ctx *c, int64_t n, const void *x, double sigma_hint = 0.0)
     }
     c->launches = 0;
     cudaEventRecord(c->ev[0], c->stream);
+    // keys, counts and the scatter into leaves; the largest leaf sizes the per-leaf sort
     if ((st = launch_tree(c, x))) return st;
-    cudaEventRecord(c->ev[1], c->stream);
     int ml = 0;
     cudaError_t e = cudaMemcpyAsync(&ml, c->maxleaf.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "read leaf occupancy");
@@ -430,6 +430,9 @@ int build_impl(Ctx *c, int64_t n, const void *x, double sigma_hint = 0.0)
     c->max_leaf = ml;
     if (ml > LEAF_SORT_CAP)
         return fail(c, VFMM_ERR_UNSUPPORTED, "a leaf holds more particles than the per-leaf sort capacity (4096); use a deeper tree");
+    if ((st = launch_leaf_sort(c, x, ml))) return st;
+    cudaEventRecord(c->ev[1], c->stream);
+    if ((st = check_device_error(c))) return st;
     c->built = true;
     return VFMM_OK;
 }

@@ -135,7 +135,7 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
                             float4 *__restrict__ bbox, int *__restrict__ oct_start, float4 *__restrict__ oct_box,
                             int *__restrict__ err)
 {
-    __shared__ unsigned long long s[LEAF_SORT_CAP];
+    extern __shared__ unsigned long long s[];  // next power of two >= the largest leaf
     __shared__ int ocnt[8], omin[8][3], omax[8][3];
     int leaf = blockIdx.x;
     int b = start[leaf], e = start[leaf + 1];
@@ -164,8 +164,9 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
         return;
     }
     const int cz = leaf % nside, cy = (leaf / nside) % nside, cx = leaf / (nside * nside);
-    const double invL = 1.0 / L;
-    const double s2 = 2.0 * nside * invL;
+    // the input's own precision, as for the leaf keys
+    const TIn Lt = (TIn)L, invL = (TIn)(1.0 / L);
+    const TIn s2 = (TIn)(2.0 * nside / L);
     int m = 1;
     while (m < cnt) m <<= 1;
     __syncthreads();
@@ -176,7 +177,7 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
             int o = 0;
             const int cc[3] = {cx, cy, cz};
             for (int d = 0; d < 3; ++d) {
-                double v = wrap_coord<double>((double)x[3 * (int64_t)i + d], L, invL);
+                TIn v = wrap_coord<TIn>(x[3 * (int64_t)i + d], Lt, invL);
                 int h = (int)(v * s2) - 2 * cc[d];
                 h = h < 0 ? 0 : (h > 1 ? 1 : h);
                 o = 2 * o + h;
@@ -206,9 +207,9 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
         int i = (int)(unsigned)(key & 0xffffffffull);
         int o = (int)(key >> 32);
         perm[b + k] = i;
-        T c0 = (T)wrap_coord<double>((double)x[3 * (int64_t)i + 0], L, invL);
-        T c1 = (T)wrap_coord<double>((double)x[3 * (int64_t)i + 1], L, invL);
-        T c2 = (T)wrap_coord<double>((double)x[3 * (int64_t)i + 2], L, invL);
+        T c0 = (T)wrap_coord<TIn>(x[3 * (int64_t)i + 0], Lt, invL);
+        T c1 = (T)wrap_coord<TIn>(x[3 * (int64_t)i + 1], Lt, invL);
+        T c2 = (T)wrap_coord<TIn>(x[3 * (int64_t)i + 2], Lt, invL);
         xs[b + k] = make_v4<T>(c0, c1, c2, T(0));
         // boxes of the FP32-rounded positions the P2P kernel sees
         float cf[3] = {(float)c0, (float)c1, (float)c2};
@@ -261,11 +262,32 @@ template <typename TIn, typename T> static int tree_impl(Ctx *c, const TIn *x)
     k_scan_parts<<<1, 1024, 0, st>>>(nparts, part, start + nleaf);
     k_scan_add<<<(int)((nleaf + 255) / 256), 256, 0, st>>>(nleaf, start, part);
     k_scatter<<<nb, 256, 0, st>>>(n, (int *)c->keys.p, start, (int *)c->fill.p, (int *)c->tmpidx.p);
-    k_leaf_sort<TIn, T><<<(unsigned)nleaf, 64, 0, st>>>(start, (int *)c->tmpidx.p, x, c->cfg.box, c->nside,
-                                                         (int *)c->perm.p, (typename V4<T>::type *)c->xs.p,
-                                                         (float4 *)c->bbox.p, (int *)c->oct_start.p,
-                                                         (float4 *)c->oct_box.p, (int *)c->err.p);
-    c->launches += 5;  // k_keys, three scan kernels and k_scatter precede k_leaf_sort
+    c->launches += 4;  // k_keys, three scan kernels precede k_scatter
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+template <typename TIn, typename T> static int leaf_sort_impl(Ctx *c, const TIn *x, int max_leaf)
+{
+    int m = 1;
+    while (m < max_leaf) m <<= 1;
+    const size_t sm = (size_t)m * sizeof(unsigned long long);
+    static bool attr[2] = {false, false};
+    const int ai = sizeof(TIn) == 8 ? 1 : 0;
+    if (!attr[ai]) {
+        cudaError_t e = cudaFuncSetAttribute(k_leaf_sort<TIn, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(LEAF_SORT_CAP * sizeof(unsigned long long)));
+        if (e != cudaSuccess) {
+            c->last_error = std::string("leaf sort shared memory: ") + cudaGetErrorString(e);
+            return VFMM_ERR_CUDA;
+        }
+        attr[ai] = true;
+    }
+    int *start = (int *)c->leaf_start.p;
+    k_leaf_sort<TIn, T><<<(unsigned)c->nleaf, 64, sm, c->stream>>>(start, (int *)c->tmpidx.p, x, c->cfg.box, c->nside,
+                                                                  (int *)c->perm.p, (typename V4<T>::type *)c->xs.p,
+                                                                  (float4 *)c->bbox.p, (int *)c->oct_start.p,
+                                                                  (float4 *)c->oct_box.p, (int *)c->err.p);
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
 }
@@ -274,6 +296,12 @@ int launch_tree(Ctx *c, const void *x)
 {
     if (c->f64) return tree_impl<double, double>(c, (const double *)x);
     return tree_impl<float, float>(c, (const float *)x);
+}
+
+int launch_leaf_sort(Ctx *c, const void *x, int max_leaf)
+{
+    if (c->f64) return leaf_sort_impl<double, double>(c, (const double *)x, max_leaf);
+    return leaf_sort_impl<float, float>(c, (const float *)x, max_leaf);
 }
 
 }  // namespace vfmm

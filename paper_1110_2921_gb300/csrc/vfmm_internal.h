@@ -125,7 +125,8 @@ struct Ctx {
 };
 
 // kernels.cu entry points (host launchers)
-int launch_tree(Ctx *c, const void *x);
+int launch_tree(Ctx *c, const void *x);  // keys, counts, scan, scatter into leaves
+int launch_leaf_sort(Ctx *c, const void *x, int max_leaf);  // per-leaf octant order, boxes
 int launch_gather_gamma(Ctx *c, const void *gamma);
 int launch_p2m(Ctx *c);
 int launch_gemm(Ctx *c, const GemmParams &gp, int ngroups, int64_t ncell_group);
