@@ -260,11 +260,25 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
     }
     c->last_R = R;
     c->last_Rc = Rc;
-    cudaStream_t st = c->stream;
+    cudaStream_t main_st = c->stream;
     int rc;
-    cudaEventRecord(c->ev[2], st);
+    cudaEventRecord(c->ev[2], main_st);
     if ((rc = launch_gather_gamma(c, gamma))) return rc;
     const void *uf = nullptr, *sf = nullptr;
+    // FP32 velocity / stretching: the far field runs on a high-priority side stream while the
+    // P2P (near field only) runs on the caller's stream; a last kernel adds the far field
+    const bool overlap = fmm && !grad && !c->f64 && c->overlap && c->side;
+    if (overlap) {
+        cudaEventRecord(c->ev[11], main_st);
+        cudaStreamWaitEvent(c->side, c->ev[11], 0);
+        c->stream = c->side;
+    }
+    cudaStream_t st = c->stream;
+    struct Restore {
+        Ctx *c;
+        cudaStream_t s;
+        ~Restore() { c->stream = s; }
+    } restore{c, main_st};
     if (fmm) {
         const int D = c->depth;
         const int S = c->cfg.periodic_levels;
@@ -341,18 +355,27 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
         }
         cudaEventRecord(c->ev[7], st);
         if ((rc = launch_l2p(c, grad))) return rc;
+        cudaEventRecord(c->ev[10], st);
         uf = c->ufar.p;
         sf = grad ? c->gfar.p : c->sfar.p;
     } else {
         for (int k = 3; k <= 7; ++k) cudaEventRecord(c->ev[k], st);
+        cudaEventRecord(c->ev[10], st);
     }
-    cudaEventRecord(c->ev[8], st);
+    c->stream = main_st;
+    cudaEventRecord(c->ev[8], main_st);
     if (grad) {
         if ((rc = launch_p2p_grad(c, R, sigma, uf, sf, u_out, s_out, fmm ? -1 : c->cfg.direct_images))) return rc;
+    } else if (overlap) {
+        if ((rc = launch_p2p(c, R, Rc, sigma, nullptr, nullptr, u_out, s_out, -1))) return rc;
     } else {
         if ((rc = launch_p2p(c, R, Rc, sigma, uf, sf, u_out, s_out, fmm ? -1 : c->cfg.direct_images))) return rc;
     }
-    cudaEventRecord(c->ev[9], st);
+    cudaEventRecord(c->ev[9], main_st);
+    if (overlap) {
+        cudaStreamWaitEvent(main_st, c->ev[10], 0);
+        if ((rc = launch_add_far(c, u_out, s_out))) return rc;
+    }
     c->timed_eval = true;
     return VFMM_OK;
 }
@@ -493,7 +516,7 @@ int vfmm_create(const vfmm_config *cfg, vfmm_handle *out)
     c->p = k.method == VFMM_METHOD_FMM ? k.p : 2;
     c->nc = (c->p + 1) * (c->p + 1);
     c->pc = ((c->nc + 31) / 32) * 32;
-    for (int i = 0; i < 10; ++i) {
+    for (int i = 0; i < 12; ++i) {
         if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
             cudaGetLastError();
             delete h;
@@ -501,6 +524,14 @@ int vfmm_create(const vfmm_config *cfg, vfmm_handle *out)
         }
     }
     c->have_events = true;
+    {
+        int lo = 0, hi = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi) != cudaSuccess) {
+            cudaGetLastError();
+            c->side = nullptr;  // the far field then runs in line with the P2P
+        }
+    }
     int st = ensure(c, c->err, sizeof(int), "error word");
     if (!st && cudaMemset(c->err.p, 0, sizeof(int)) != cudaSuccess) st = VFMM_ERR_CUDA;
     if (!st && k.method == VFMM_METHOD_FMM) {
@@ -526,7 +557,8 @@ int vfmm_destroy(vfmm_handle h)
                       &c->lattice_f64, &c->root_m, &c->kblocks, &c->cls, &c->hx, &c->hg, &c->hu, &c->hs};
     for (DevBuf *b : bufs) release(*b);
     if (c->have_events)
-        for (int i = 0; i < 10; ++i) cudaEventDestroy(c->ev[i]);
+        for (int i = 0; i < 12; ++i) cudaEventDestroy(c->ev[i]);
+    if (c->side) cudaStreamDestroy(c->side);
     delete h;
     return VFMM_OK;
 }
@@ -703,7 +735,8 @@ int vfmm_get_timings(vfmm_handle h, double *ms, int nphase)
     if (!h || !ms || nphase < 0) return VFMM_ERR_ARG;
     Ctx *c = &h->c;
     if (!c->timed_eval) return fail(c, VFMM_ERR_NOT_BUILT, "no evaluation has been timed");
-    const int pairs[8][2] = {{0, 1}, {2, 3}, {3, 4}, {5, 6}, {4, 5}, {6, 7}, {7, 8}, {8, 9}};
+    // L2P ends at [10]; with the far field on the side stream the phases overlap the P2P
+    const int pairs[8][2] = {{0, 1}, {2, 3}, {3, 4}, {5, 6}, {4, 5}, {6, 7}, {7, 10}, {8, 9}};
     for (int i = 0; i < nphase && i < NPHASE; ++i) {
         float t = 0.f;
         cudaError_t e = cudaEventElapsedTime(&t, c->ev[pairs[i][0]], c->ev[pairs[i][1]]);

@@ -745,3 +745,29 @@ int launch_l2p(Ctx *c, bool grad)
 }
 
 }  // namespace vfmm
+
+namespace vfmm {
+
+__global__ void k_add_far(int64_t n, const int *__restrict__ perm, const float *__restrict__ ufar,
+                          const float *__restrict__ sfar, float *__restrict__ u_out, float *__restrict__ s_out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t j = perm[i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u_out[3 * j + d] += ufar[3 * i + d];
+    if (s_out)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) s_out[3 * j + d] += sfar[3 * i + d];
+}
+
+int launch_add_far(Ctx *c, void *u_out, void *s_out)
+{
+    const int nb = (int)((c->n + 255) / 256);
+    k_add_far<<<nb, 256, 0, c->stream>>>(c->n, (const int *)c->perm.p, (const float *)c->ufar.p, (const float *)c->sfar.p,
+                                         (float *)u_out, (float *)s_out);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+}  // namespace vfmm

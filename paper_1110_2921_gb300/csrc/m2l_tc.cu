@@ -348,8 +348,11 @@ constexpr int TL_CELLS = 128;              // target cells per CTA (whole z-line
 constexpr int TL_N = 3 * TL_CELLS;         // accumulator columns
 constexpr int TL_HALO = 2;                 // |shz| <= 2
 constexpr int TL_MAXOFF = 3;               // offsets per class (the z parity leaves at most three)
-constexpr int TL_STAGES = 4;
-constexpr int TL_PF = 2;
+#ifndef VFMM_TL_STAGES
+#define VFMM_TL_STAGES 3
+#endif
+constexpr int TL_STAGES = VFMM_TL_STAGES;
+constexpr int TL_PF = TL_STAGES >= 4 ? 2 : 1;
 constexpr int TL_MAXCLS = 96;
 constexpr int TL_TMEM_COLS = 512;
 constexpr int TL_THREADS = 32 + TC_THREADS;  // MMA warp + 4 producer warps

@@ -116,7 +116,9 @@ struct Ctx {
     int cls_off[3][8], cls_cnt[3][8];        // in classes (three int4 each)
     int kb_m2m_off = 0, kb_l2l_off[8];
 
-    cudaEvent_t ev[10];
+    cudaEvent_t ev[12];            // [10] far field done (side stream), [11] fork
+    cudaStream_t side = nullptr;   // high-priority stream of the far field when it overlaps the P2P
+    bool overlap = true;           // FP32 velocity/stretching: far field concurrent with the P2P
     bool have_events = false;
     bool timed_eval = false;
     int64_t launches = 0;      // kernels launched by the last build + evaluation
@@ -132,6 +134,8 @@ int launch_p2m(Ctx *c);
 int launch_gemm(Ctx *c, const GemmParams &gp, int ngroups, int64_t ncell_group);
 int launch_root(Ctx *c);
 int launch_l2p(Ctx *c, bool grad);
+// u_out[perm[i]] += ufar[i], s_out[perm[i]] += sfar[i] (FP32)
+int launch_add_far(Ctx *c, void *u_out, void *s_out);
 int launch_p2p_grad(Ctx *c, int R, double sigma, const void *ufar, const void *gfar, void *u_out, void *g_out,
                     int direct_K);
 int launch_adjoint_combine(Ctx *c, const void *G1, const void *w, const void *G2, const void *gamma, void *dx);
