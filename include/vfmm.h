@@ -88,12 +88,15 @@ typedef struct vfmm_config {
     int method;          /* VFMM_METHOD_FMM | VFMM_METHOD_DIRECT */
     int direct_images;   /* K for VFMM_METHOD_DIRECT */
     void *stream;        /* cudaStream_t */
+    int concurrent_far;  /* 1 (default): in the FP32 velocity / stretching evaluation the far field runs on an
+                          * internal high-priority stream while the near-field P2P runs on `stream`, joined
+                          * before the far field is added; 0: every phase in line on `stream` */
 } vfmm_config;
 
 typedef struct vfmm_ctx *vfmm_handle;
 
 /* Fill *cfg with defaults: p=10, depth=0, ncrit=64, near_rings=0, rho_cut=5, S=2, L=2 pi,
- * F32, M2L BF16X3, FMM, K=1, stream NULL. */
+ * F32, M2L BF16X3, FMM, K=1, stream NULL, concurrent_far 1. */
 int vfmm_config_default(vfmm_config *cfg);
 
 /* Create a handle; precomputes the FP64 translation and lattice operators on the host and

@@ -19,7 +19,7 @@ PHASES = ["tree", "p2m", "m2m", "m2l", "periodic", "l2l", "l2p", "p2p"]
 
 def make_config(p=10, depth=0, ncrit=64, near_rings=0, rho_cut=5.0, periodic_levels=2,
                 box=2 * math.pi, dtype="f32", m2l="bf16x3", method="fmm", direct_images=1,
-                stream=None):
+                stream=None, concurrent_far=1):
     c = config_default()
     c.p = p
     c.depth = depth
@@ -35,6 +35,7 @@ def make_config(p=10, depth=0, ncrit=64, near_rings=0, rho_cut=5.0, periodic_lev
     c.method = _native.VFMM_METHOD_DIRECT if method == "direct" else _native.VFMM_METHOD_FMM
     c.direct_images = direct_images
     c.stream = stream
+    c.concurrent_far = int(concurrent_far)
     return c
 
 

@@ -33,7 +33,8 @@ class vfmm_config(ctypes.Structure):
                 ("near_rings", ctypes.c_int), ("rho_cut", ctypes.c_double),
                 ("periodic_levels", ctypes.c_int), ("box", ctypes.c_double),
                 ("dtype", ctypes.c_int), ("m2l_prec", ctypes.c_int), ("method", ctypes.c_int),
-                ("direct_images", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("direct_images", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("concurrent_far", ctypes.c_int)]
 
 
 class VfmmError(RuntimeError):

@@ -473,6 +473,7 @@ int vfmm_config_default(vfmm_config *cfg)
     cfg->ncrit = 64;
     cfg->near_rings = 0;
     cfg->rho_cut = 5.0;
+    cfg->concurrent_far = 1;
     cfg->periodic_levels = 2;
     cfg->box = 6.283185307179586477;
     cfg->dtype = VFMM_F32;
@@ -511,6 +512,7 @@ int vfmm_create(const vfmm_config *cfg, vfmm_handle *out)
     Ctx *c = &h->c;
     c->cfg = k;
     c->stream = (cudaStream_t)k.stream;
+    c->overlap = k.concurrent_far != 0;
     c->f64 = k.dtype == VFMM_F64;
     c->esz = c->f64 ? 8 : 4;
     c->p = k.method == VFMM_METHOD_FMM ? k.p : 2;

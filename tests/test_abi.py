@@ -45,5 +45,5 @@ def test_host_only_calls():
 
 def test_layout_matches_header():
     from paper_1110_2921_gb300 import _native as nv
-    # vfmm_config: 4 ints, double, int, double, 4 ints, pointer
-    assert ctypes.sizeof(nv.vfmm_config) == 4 * 4 + 8 + 8 + 8 + 4 * 4 + 8
+    # vfmm_config: 4 ints, double, int, double, 4 ints, pointer, int (padded to 8)
+    assert ctypes.sizeof(nv.vfmm_config) == 4 * 4 + 8 + 8 + 8 + 4 * 4 + 8 + 8
