@@ -470,44 +470,61 @@ int launch_split_reduce(Ctx *c, int nsplit, int64_t count, const void *partial, 
 // Root step in FP64: M_0 = sum_b M2M_b M_1[b]; L_0 = Op M_0 with Op the periodic lattice
 // operator (images outside the central 3^3 boxes; Section 3.1 last paragraph).
 template <typename T>
-__global__ void k_root(const T *__restrict__ M1, const double *__restrict__ m2m, const double *__restrict__ op,
-                       int nc, int pc, double *__restrict__ root_m, T *__restrict__ L0)
+__global__ void k_root_m2m(const T *__restrict__ M1, const double *__restrict__ m2m, int nc, int pc,
+                           double *__restrict__ root_m)
 {
-    extern __shared__ double rm[];  // [3][nc]
-    for (int o = threadIdx.x; o < 3 * nc; o += blockDim.x) {
-        int comp = o / nc, k = o - comp * nc;
-        double s = 0.0;
-        for (int b = 0; b < 8; ++b) {
-            const double *A = m2m + ((size_t)b * nc + k) * nc;
-            const T *x = M1 + ((size_t)b * 3 + comp) * pc;
-            for (int j = 0; j < nc; ++j) s += A[j] * (double)x[j];
-        }
-        rm[o] = s;
-        root_m[o] = s;
+    // one warp per root coefficient (k, comp): sum over the 8 children and j, lanes along j
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (o >= 3 * nc) return;
+    const int comp = o / nc, k = o - comp * nc;
+    double s = 0.0;
+    for (int b = 0; b < 8; ++b) {
+        const double *A = m2m + ((size_t)b * nc + k) * nc;
+        const T *x = M1 + ((size_t)b * 3 + comp) * pc;
+        for (int j = lane; j < nc; j += 32) s += A[j] * (double)x[j];
     }
-    __syncthreads();
-    for (int o = threadIdx.x; o < 3 * pc; o += blockDim.x) {
-        int comp = o / pc, k = o - comp * pc;
-        double s = 0.0;
-        if (k < nc) {
-            const double *A = op + (size_t)k * nc;
-            for (int j = 0; j < nc; ++j) s += A[j] * rm[comp * nc + j];
-        }
-        L0[o] = (T)s;
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) root_m[o] = s;
+}
+
+template <typename T>
+__global__ void k_root_lattice(const double *__restrict__ op, const double *__restrict__ root_m, int nc, int pc,
+                               T *__restrict__ L0)
+{
+    // L_0 = Op M_0, one warp per output (k, comp) (k >= nc: zero padding)
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (o >= 3 * pc) return;
+    const int comp = o / pc, k = o - comp * pc;
+    double s = 0.0;
+    if (k < nc) {
+        const double *A = op + (size_t)k * nc;
+        for (int j = lane; j < nc; j += 32) s += A[j] * root_m[comp * nc + j];
     }
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) L0[o] = (T)s;
 }
 
 int launch_root(Ctx *c)
 {
-    size_t sm = 3 * c->nc * sizeof(double);
-    if (c->f64)
-        k_root<double><<<1, 384, sm, c->stream>>>((const double *)c->mexp.p + c->lvl_off[1],
-                                                  (const double *)c->m2m_f64.p, (const double *)c->lattice_f64.p,
-                                                  c->nc, c->pc, (double *)c->root_m.p, (double *)c->lexp.p);
-    else
-        k_root<float><<<1, 384, sm, c->stream>>>((const float *)c->mexp.p + c->lvl_off[1],
-                                                 (const double *)c->m2m_f64.p, (const double *)c->lattice_f64.p,
-                                                 c->nc, c->pc, (double *)c->root_m.p, (float *)c->lexp.p);
+    const int wpb = 8;  // warps per block
+    const unsigned nb1 = (unsigned)((3 * c->nc + wpb - 1) / wpb), nb2 = (unsigned)((3 * c->pc + wpb - 1) / wpb);
+    if (c->f64) {
+        k_root_m2m<double><<<nb1, 32 * wpb, 0, c->stream>>>((const double *)c->mexp.p + c->lvl_off[1],
+                                                             (const double *)c->m2m_f64.p, c->nc, c->pc,
+                                                             (double *)c->root_m.p);
+        VFMM_CUDA_CHECK_LAUNCH(c);
+        k_root_lattice<double><<<nb2, 32 * wpb, 0, c->stream>>>((const double *)c->lattice_f64.p,
+                                                                 (const double *)c->root_m.p, c->nc, c->pc,
+                                                                 (double *)c->lexp.p);
+    } else {
+        k_root_m2m<float><<<nb1, 32 * wpb, 0, c->stream>>>((const float *)c->mexp.p + c->lvl_off[1],
+                                                            (const double *)c->m2m_f64.p, c->nc, c->pc,
+                                                            (double *)c->root_m.p);
+        VFMM_CUDA_CHECK_LAUNCH(c);
+        k_root_lattice<float><<<nb2, 32 * wpb, 0, c->stream>>>((const double *)c->lattice_f64.p,
+                                                                (const double *)c->root_m.p, c->nc, c->pc,
+                                                                (float *)c->lexp.p);
+    }
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
 }
@@ -520,7 +537,9 @@ int launch_root(Ctx *c)
 // i.e. for psi = sum conj(Y_k^l) F_k^l:
 //   G^z_{a,b} = F_{a+1,b},  G^x_{a,b} = (F_{a+1,b-1} - F_{a+1,b+1})/2,
 //   G^y_{a,b} = i (F_{a+1,b+1} + F_{a+1,b-1})/2.
-// Each particle then evaluates Y_a^b at its offset once and accumulates 27 dot products.
+// The kernel turns these into the velocity tables U_a = eps_abc D^b Psi_c and their
+// gradients D^k U_a; each particle evaluates Y_a^b at its offset once and accumulates 12
+// table dot products.
 constexpr int L2P_BS = 64;   // one thread per particle of a 64-particle leaf
 constexpr int NCX_MAX = (PMAX + 1) * (PMAX + 2) / 2;
 __constant__ unsigned char c_cn[NCX_MAX], c_cm[NCX_MAX];  // complex index -> (n, m)

@@ -177,3 +177,13 @@ def test_ring_two_correction_off_lattice(sigma_over_h):
         eu1, es1 = rel_l2(u1[tid], uo), rel_l2(s1[tid], so)
         print("uncorrected: u %.3e S %.3e" % (eu1, es1))
         assert eu1 > 3 * eu and es1 > 3 * es
+
+
+def test_concurrent_far_field_matches_in_line():
+    # the far field on the side stream, added after the P2P, gives the same FP32 sums as the
+    # in-line order (near field, then far field added in the P2P epilogue): bitwise
+    f = wl.make_vortex_lattice(32, 4, 1)
+    kw = dict(p=10, depth=3, periodic_levels=2, m2l="bf16x3")
+    u1, s1, _ = run_fmm(f["x"], f["alpha"], f["sigma"], concurrent_far=1, **kw)
+    u0, s0, _ = run_fmm(f["x"], f["alpha"], f["sigma"], concurrent_far=0, **kw)
+    assert np.array_equal(u1, u0) and np.array_equal(s1, s0)
