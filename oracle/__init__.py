@@ -13,6 +13,8 @@ Contents
 * ``gradient``: dL/dgamma and dL/dx of L = sum |u - u*|^2 from the direct sums.
 * ``integrate``: one Heun step of Eqs. (convection), (stretching), (csm); FP64 diagnostics.
 * ``reinit``: Gaussian-basis reinitialisation onto a lattice (dense FP64, small lattices).
+* ``diagnostics``: energy spectrum of a lattice velocity field, skewness and flatness of the
+  velocity derivatives (Section 5.2).
 
 Parity status: every function here is pinned by the ``tests/test_oracle_*.py`` checks
 (closed forms, quadrature, mpmath brute force, invariants, spectral cross-check).
@@ -102,3 +104,4 @@ from . import spectral  # noqa: E402,F401
 from . import gradient  # noqa: E402,F401
 from . import integrate  # noqa: E402,F401
 from . import reinit  # noqa: E402,F401
+from . import diagnostics  # noqa: E402,F401

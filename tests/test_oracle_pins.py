@@ -355,3 +355,76 @@ def test_reinit_residual_decreases():
     g = np.random.default_rng(52).normal(size=x.shape) * h ** 3
     res = [oracle.reinit.reinit(x, g, 1.1 * h, m, iters=k)[2] for k in (0, 1, 5, 20)]
     assert res[0] > res[1] > res[2] > res[3]
+
+
+# ---------------------------------------------------------------------------------------
+# Diagnostics of Section 5.2 (energy spectrum, derivative skewness and flatness)
+
+def test_spectrum_single_mode_closed_form():
+    # u_y = sin(m x): u_hat = -+i/2 at k = +-m e_x, so E(m) = 2 * 0.5 * 1/4 = 1/4 and
+    # nothing else; 0.5 <u^2> = 1/4 as well
+    n, m = 16, 3
+    x = wl.lattice_positions(n)
+    u = np.zeros((n ** 3, 3))
+    u[:, 1] = np.sin(m * x[:, 0])
+    E = oracle.diagnostics.energy_spectrum(u, n, 14)
+    ref = np.zeros(15)
+    ref[m] = 0.25
+    assert np.allclose(E, ref, atol=1e-14)
+
+
+def test_spectrum_oblique_mode_shell():
+    # a mode along (1, 2, 2) has |k| = 3 exactly; one along (2, 2, 1) too; (1, 1, 1) lands in
+    # shell round(sqrt 3) = 2
+    n = 16
+    x = wl.lattice_positions(n)
+    u = np.zeros((n ** 3, 3))
+    u[:, 0] = np.cos(x @ np.array([1.0, 2.0, 2.0]))
+    u[:, 2] = 2.0 * np.cos(x @ np.array([1.0, 1.0, 1.0]))
+    E = oracle.diagnostics.energy_spectrum(u, n, 14)
+    assert abs(E[3] - 0.25) < 1e-13 and abs(E[2] - 1.0) < 1e-13
+    assert abs(E.sum() - 1.25) < 1e-13
+
+
+def test_spectrum_parseval_random_field():
+    n = 16
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal((n ** 3, 3))
+    E = oracle.diagnostics.energy_spectrum(u, n, int(np.ceil(np.sqrt(3) * n / 2)) + 1)
+    assert abs(E.sum() - 0.5 * (u ** 2).sum(1).mean()) < 1e-12 * E.sum()
+
+
+def test_spectrum_of_generated_field_is_the_prescribed_spectrum():
+    # the generator rescales every integer shell to k^4 exp(-2 k^2/k0^2) (Eq. initspec) with
+    # unit energy; the lattice FFT of its velocity recovers exactly that (no aliasing: the
+    # modes stay inside |k_i| <= n/2 - 1)
+    n, k0 = 32, 4
+    u = wl.lattice_velocity(n, k0, seed=1)
+    E = oracle.diagnostics.energy_spectrum(u, n, 27)
+    s = np.arange(28, dtype=np.float64)
+    tgt = s ** 4 * np.exp(-2.0 * s ** 2 / k0 ** 2)
+    smax = int(np.rint(np.sqrt(3) * min(4 * k0, n // 2 - 1)))
+    tgt[smax + 1:] = 0.0
+    tgt /= tgt.sum()
+    assert np.allclose(E, tgt, rtol=1e-10, atol=1e-14)
+
+
+def test_derivative_moments_closed_form():
+    # u = (sin x, sin y, sin z): du_a/dx_a = cos of the coordinate; on a lattice of n >= 5
+    # points the sample means of cos^2, cos^3, cos^4 are 1/2, 0, 3/8: F3 = 0, F4 = 3/2
+    n = 12
+    x = wl.lattice_positions(n)
+    g = np.zeros((n ** 3, 9))
+    g[:, 0], g[:, 4], g[:, 8] = np.cos(x[:, 0]), np.cos(x[:, 1]), np.cos(x[:, 2])
+    g[:, 1] = 5.0  # off-diagonal entries are not samples
+    m2, m3, m4, F3, F4 = oracle.diagnostics.derivative_moments(g)
+    assert abs(m2 - 0.5) < 1e-14 and abs(m3) < 1e-14 and abs(m4 - 0.375) < 1e-14
+    assert abs(F3) < 1e-13 and abs(F4 - 1.5) < 1e-13
+
+
+def test_derivative_moments_gaussian_samples():
+    # normal samples: F3 -> 0, F4 -> 3 (statistical: 3e6 samples, 5-sigma bounds)
+    rng = np.random.default_rng(11)
+    g = rng.standard_normal((1_000_000, 9))
+    _, _, _, F3, F4 = oracle.diagnostics.derivative_moments(g)
+    assert abs(F3) < 5 * np.sqrt(15.0 / 3e6) and abs(F4 - 3.0) < 5 * np.sqrt(96.0 / 3e6)
