@@ -173,6 +173,24 @@ int vfmm_reinit(vfmm_handle h, int64_t n, const void *x, const void *gamma, doub
  * out[7] = sum |gamma|^2.  Synchronises the stream. */
 int vfmm_diagnostics(vfmm_handle h, int64_t n, const void *x, const void *gamma, const void *u, double *out);
 
+/* Energy spectrum of a velocity field sampled on the n^3 lattice (Section 5.2 evaluates the
+ * velocity on a lattice with the Biot-Savart law and takes a 3-D FFT):
+ *   E(k) = sum over integer wave vectors with k - 1/2 <= |k| < k + 1/2 of 0.5 |u_hat(k)|^2,
+ *   u_hat(k) = n^-3 sum_x u(x) exp(-i k.x),  k = 0..kmax,
+ * so that sum_k E(k) = 0.5 <|u|^2> once kmax >= sqrt(3) n / 2.  u_lattice: device n^3 x 3 of the
+ * configured dtype in lattice order (ix n + iy) n + iz (the order of a lattice particle set);
+ * n a power of two in [4, 1024]; 0 <= kmax <= 4096.  E_out: host, kmax + 1 doubles.  FP64
+ * throughout; the handle keeps a 48 n^3-byte workspace after the first call.  Synchronises
+ * the stream.  Errors: bad pointers or kmax -> VFMM_ERR_ARG; other n -> VFMM_ERR_UNSUPPORTED. */
+int vfmm_energy_spectrum(vfmm_handle h, int n, const void *u_lattice, int kmax, double *E_out);
+
+/* Velocity-derivative moments (Section 5.2: F_n = mean(u_x^n) / mean(u_x^2)^(n/2), F_3 the
+ * skewness, F_4 the flatness).  The samples are the three longitudinal derivatives
+ * du_a/dx_a of each particle (isotropy), read from a gradient g (device n x 9, g[9 i + 3 a + k]
+ * = du_a/dx_k, as vfmm_eval_velocity_gradient writes it).  out (host, 5 doubles): mean d^2,
+ * mean d^3, mean d^4, F_3, F_4, accumulated in FP64.  Synchronises the stream. */
+int vfmm_derivative_moments(vfmm_handle h, int64_t n, const void *grad, double *out);
+
 /* End to end from HOST memory: copies x and gamma to the device, builds the tree,
  * evaluates, copies u and S back, and synchronises.  Pointers are host n x 3 arrays of the
  * configured dtype; s_out may be NULL. */

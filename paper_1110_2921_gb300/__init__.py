@@ -10,6 +10,7 @@ from ._native import (VfmmError, vfmm_create, vfmm_destroy, vfmm_build_tree,  # 
                       vfmm_eval_velocity_stretching, vfmm_eval_host, vfmm_sync,
                       vfmm_get_timings, vfmm_get_tree_info, vfmm_set_stream, config_default,
                       vfmm_eval_velocity_gradient, vfmm_eval_adjoint, vfmm_rk_step, vfmm_diagnostics,
+                      vfmm_energy_spectrum, vfmm_derivative_moments,
                       vfmm_reinit)
 
 PRECISIONS = {"fp32": _native.VFMM_M2L_FP32, "fp64": _native.VFMM_M2L_FP64,
@@ -136,6 +137,18 @@ class VortexFMM:
         vfmm_set_stream(self.h, self.torch.cuda.current_stream().cuda_stream)
         v = vfmm_diagnostics(self.h, x.shape[0], x.data_ptr(), gamma.data_ptr(), u.data_ptr() if u is not None else 0)
         return {"total_vorticity": v[0:3], "x_cross_gamma": v[3:6], "sum_u2": v[6], "sum_gamma2": v[7]}
+
+    def energy_spectrum(self, u_lattice, n, kmax):
+        """E(k), k = 0..kmax, of a velocity sampled on the n^3 lattice (device (n^3, 3), lattice order)."""
+        self._check(u_lattice)
+        return vfmm_energy_spectrum(self.h, n, u_lattice.data_ptr(), kmax)
+
+    def derivative_moments(self, grad):
+        """(mean d^2, mean d^3, mean d^4, F3, F4) of the longitudinal derivatives of grad (n, 9)."""
+        if not (grad.is_cuda and grad.dtype == self.dtype and grad.is_contiguous() and grad.dim() == 2
+                and grad.shape[1] == 9):
+            raise ValueError("expected a contiguous CUDA (n, 9) tensor of %s" % self.dtype)
+        return vfmm_derivative_moments(self.h, grad.shape[0], grad.data_ptr())
 
     def __call__(self, x, gamma, sigma, stretching=True):
         self.build_tree(x)

@@ -68,6 +68,8 @@ def lib():
             "vfmm_rk_step": ([H, ctypes.c_int64, V, V, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                               ctypes.c_double], ctypes.c_int),
             "vfmm_diagnostics": ([H, ctypes.c_int64, V, V, V, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "vfmm_energy_spectrum": ([H, ctypes.c_int, V, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "vfmm_derivative_moments": ([H, ctypes.c_int64, V, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "vfmm_reinit": ([H, ctypes.c_int64, V, V, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                              V, V, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "vfmm_sync": ([H], ctypes.c_int),
@@ -157,6 +159,18 @@ def vfmm_diagnostics(h, n, x_ptr, gamma_ptr, u_ptr):
     out = (ctypes.c_double * 8)()
     check(lib().vfmm_diagnostics(h, int(n), ctypes.c_void_p(x_ptr), ctypes.c_void_p(gamma_ptr),
                                  ctypes.c_void_p(u_ptr) if u_ptr else None, out), "vfmm_diagnostics", h)
+    return list(out)
+
+
+def vfmm_energy_spectrum(h, n, u_ptr, kmax):
+    out = (ctypes.c_double * (kmax + 1))()
+    check(lib().vfmm_energy_spectrum(h, int(n), ctypes.c_void_p(u_ptr), int(kmax), out), "vfmm_energy_spectrum", h)
+    return list(out)
+
+
+def vfmm_derivative_moments(h, n, g_ptr):
+    out = (ctypes.c_double * 5)()
+    check(lib().vfmm_derivative_moments(h, int(n), ctypes.c_void_p(g_ptr), out), "vfmm_derivative_moments", h)
     return list(out)
 
 

@@ -13,7 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvfmm.so")
-SOURCES = ["api.cu", "operators.cpp", "tree.cu", "p2p.cu", "expansions.cu", "m2l_tc.cu", "integrate.cu", "reinit.cu"]
+SOURCES = ["api.cu", "operators.cpp", "tree.cu", "p2p.cu", "expansions.cu", "m2l_tc.cu", "integrate.cu", "reinit.cu",
+           "diagnostics.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

@@ -556,7 +556,7 @@ int vfmm_destroy(vfmm_handle h)
     DevBuf *bufs[] = {&c->xs, &c->gs, &c->perm, &c->keys, &c->leaf_start, &c->counts, &c->fill, &c->tmpidx,
                       &c->scan_part, &c->err, &c->maxleaf, &c->bbox, &c->oct_start, &c->oct_box, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->gemm_part, &c->ufar,
                       &c->sfar, &c->gfar, &c->adj_u, &c->adj_g1, &c->adj_g2, &c->rk_u1, &c->rk_s1, &c->rk_u2, &c->rk_s2, &c->rk_x1, &c->rk_g1, &c->diag, &c->rg_om, &c->rg_r, &c->rg_d, &c->rg_q, &c->rg_t1, &c->rg_t2, &c->rg_dots, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->m2m_f64,
-                      &c->lattice_f64, &c->root_m, &c->kblocks, &c->cls, &c->hx, &c->hg, &c->hu, &c->hs};
+                      &c->lattice_f64, &c->root_m, &c->kblocks, &c->cls, &c->spec_work, &c->spec_E, &c->hx, &c->hg, &c->hu, &c->hs};
     for (DevBuf *b : bufs) release(*b);
     if (c->have_events)
         for (int i = 0; i < 12; ++i) cudaEventDestroy(c->ev[i]);
@@ -695,6 +695,47 @@ int vfmm_diagnostics(vfmm_handle h, int64_t n, const void *x, const void *gamma,
     cudaError_t e = cudaMemcpyAsync(out, c->diag.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics");
+    return VFMM_OK;
+}
+
+int vfmm_energy_spectrum(vfmm_handle h, int n, const void *u_lattice, int kmax, double *E_out)
+{
+    if (!h) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    if (!u_lattice || !E_out) return fail(c, VFMM_ERR_ARG, "null u_lattice or E_out");
+    if (n < 4 || n > 1024 || (n & (n - 1))) return fail(c, VFMM_ERR_UNSUPPORTED, "n must be a power of two in [4, 1024]");
+    if (kmax < 0 || kmax > 4096) return fail(c, VFMM_ERR_ARG, "kmax must be in [0, 4096]");
+    const size_t m = (size_t)n * n * n;
+    int st;
+    if ((st = ensure(c, c->spec_work, 3 * m * sizeof(double2), "spectrum workspace"))) return st;
+    if ((st = ensure(c, c->spec_E, (size_t)(kmax + 1) * sizeof(double), "spectrum shells"))) return st;
+    if ((st = launch_spectrum(c, n, u_lattice, kmax, (double2 *)c->spec_work.p, (double *)c->spec_E.p))) return st;
+    cudaError_t e = cudaMemcpyAsync(E_out, c->spec_E.p, (size_t)(kmax + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "energy spectrum");
+    return VFMM_OK;
+}
+
+int vfmm_derivative_moments(vfmm_handle h, int64_t n, const void *grad, double *out)
+{
+    if (!h) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    if (n <= 0 || !grad || !out) return fail(c, VFMM_ERR_ARG, "bad arguments");
+    int st;
+    if ((st = ensure(c, c->diag, 8 * sizeof(double), "diagnostics"))) return st;
+    cudaMemsetAsync(c->diag.p, 0, 3 * sizeof(double), c->stream);
+    if ((st = launch_moments(c, n, grad, (double *)c->diag.p))) return st;
+    double s[3];
+    cudaError_t e = cudaMemcpyAsync(s, c->diag.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "derivative moments");
+    const double cnt = 3.0 * (double)n;
+    out[0] = s[0] / cnt;
+    out[1] = s[1] / cnt;
+    out[2] = s[2] / cnt;
+    out[3] = out[1] / std::pow(out[0], 1.5);
+    out[4] = out[2] / (out[0] * out[0]);
     return VFMM_OK;
 }
 

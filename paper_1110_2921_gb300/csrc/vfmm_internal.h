@@ -96,6 +96,7 @@ struct Ctx {
     DevBuf mexp, lexp;             // all levels, T
     DevBuf mhi, mlo;               // tensor-core copies of the multipoles (largest level)
     DevBuf gemm_part;              // split-k partial results of the CUDA-core GEMM (small levels)
+    DevBuf spec_work, spec_E;      // energy spectrum: FP64 complex lattice copy, shell sums
     DevBuf ufar, sfar, gfar;       // far-field u, S (or grad u) in sorted order, T
     DevBuf adj_u, adj_g1, adj_g2;  // adjoint temporaries (caller order)
     DevBuf rk_u1, rk_s1, rk_u2, rk_s2, rk_x1, rk_g1;  // time-step temporaries (caller order)
@@ -136,6 +137,10 @@ int launch_root(Ctx *c);
 int launch_l2p(Ctx *c, bool grad);
 // u_out[perm[i]] += ufar[i], s_out[perm[i]] += sfar[i] (FP32)
 int launch_add_far(Ctx *c, void *u_out, void *s_out);
+// energy spectrum of an n^3 x 3 lattice velocity into E_dev[0..kmax] (work: 3 n^3 double2)
+int launch_spectrum(Ctx *c, int n, const void *u, int kmax, double2 *work, double *E_dev);
+// sums of d^2, d^3, d^4 over the longitudinal derivatives of an n x 9 gradient into out_dev[0..2]
+int launch_moments(Ctx *c, int64_t n, const void *g, double *out_dev);
 int launch_p2p_grad(Ctx *c, int R, double sigma, const void *ufar, const void *gfar, void *u_out, void *g_out,
                     int direct_K);
 int launch_adjoint_combine(Ctx *c, const void *G1, const void *w, const void *G2, const void *gamma, void *dx);
