@@ -345,9 +345,18 @@ def main():
                      depth=args.depth)
     stream = torch.cuda.current_stream()
 
-    def step():
+    ev_pairs = []
+
+    def step(mark=False):
         h.build_tree(X)
+        if mark:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
         h.eval(G, sigma, out=(U, S))
+        if mark:
+            b.record(stream)
+            ev_pairs.append((a, b))
 
     for _ in range(args.warmup):
         step()
@@ -363,7 +372,7 @@ def main():
     phase_ms = []
     t0.record(stream)
     for _ in range(args.steps):
-        step()
+        step(mark=True)
         h.sync()   # per-step phase timings are read from the library's own events
         phase_ms.append(h.timings())
     t1.record(stream)
@@ -371,6 +380,7 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
     ms = t0.elapsed_time(t1)
+    eval_ms = statistics.median(a.elapsed_time(b) for a, b in ev_pairs)
     clk = clocks.stop() if clocks else None
     ms_max, value = combine_ranks(ms, N, args.steps, device=dev)
 
@@ -420,6 +430,27 @@ def main():
     traffic = profiled_traffic("k_p2p_f32", ["p2p.cu"])
     phases = {k: round(statistics.mean(p[k] for p in phase_ms), 3) for k in phase_ms[0]}
 
+    # the tensor-core M2L: algorithmic flops of the 121 x 121 translations (three split
+    # products) on levels 3..D over the in-line M2L phase (which also holds levels 1-2 and the
+    # hi/lo splits)
+    nc = (args.p + 1) ** 2
+    m2l_flops = 0.0
+    for lvl in range(3, info["depth"] + 1):
+        offs = 189 if (lvl < info["depth"] or R == 1) else 91
+        m2l_flops += (8 ** lvl) * offs * 3 * nc * nc * 2 * 3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    m2l_achieved = m2l_flops / (phases_alone["m2l"] / 1e3) / 1e12
+    roof_m2l = {"bound": "tensor", "achieved": m2l_achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": m2l_achieved / bf16_peak, "kernel": "k_m2l_lines / k_m2l_tc (levels 3..D)",
+                "flops_per_eval": m2l_flops,
+                "peak_basis": "measured BF16 burst" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s",
+                "m2l_prec": args.m2l}
+
     out_err = {}
     if args.check:
         import oracle
@@ -457,6 +488,9 @@ def main():
                      "pairs_per_launch": pairs, "flops_per_launch": flops,
                      "flops_per_pair": {"smoothed": FLOPS_PER_PAIR, "singular": FLOPS_PER_PAIR_SINGULAR},
                      "peak_basis": "2 x 128 FP32 lanes x %d SMs x 2070 MHz" % sms},
+        "roofline_m2l": roof_m2l,
+        "excluding_tree_build": {"value": N / (eval_ms / 1e3), "unit": "particles/s", "ms_per_eval": eval_ms,
+                                 "note": "median over the timed steps of vfmm_eval_velocity_stretching alone"},
         "phases_ms": phases,
         "phases_ms_in_line": phases_alone,
         "far_field": "side stream concurrent with the P2P (phases_ms overlap); phases_ms_in_line: every phase in line",
