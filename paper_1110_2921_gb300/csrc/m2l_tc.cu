@@ -373,7 +373,7 @@ template <int H> struct TlGeom {
 };
 
 template <bool BF16, int H>
-__global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const int4 *__restrict__ cls, int ncls_g0)
+__global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const int4 *__restrict__ cls)
 {
     using Gm = TlGeom<H>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -390,7 +390,6 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
     const int line0 = blockIdx.x * Gm::LINES;  // first target line (px * H + py) of this CTA
     const int ncls = min(tp.kb_cnt[g], TL_MAXCLS);
     for (int q = tid; q < 3 * ncls; q += TL_THREADS) cls_s[q] = cls[3 * tp.kb_off[g] + q];
-    (void)ncls_g0;
     const int nchunk = tp.nchunk;
     const int nk = ncls * nchunk;
     const int pc = tp.pc;
@@ -724,7 +723,7 @@ template <bool BF16, int H> int launch_lines(Ctx *c, int level, int R, const TcP
     }
     const int lines = H * H;  // target z-lines per parity
     dim3 grid((unsigned)(lines / Gm::LINES), 8);
-    k_m2l_lines<BF16, H><<<grid, TL_THREADS, Gm::SMEM, c->stream>>>(tp, (const int4 *)c->cls.p, 0);
+    k_m2l_lines<BF16, H><<<grid, TL_THREADS, Gm::SMEM, c->stream>>>(tp, (const int4 *)c->cls.p);
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
 }
