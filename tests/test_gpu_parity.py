@@ -187,3 +187,44 @@ def test_concurrent_far_field_matches_in_line():
     u1, s1, _ = run_fmm(f["x"], f["alpha"], f["sigma"], concurrent_far=1, **kw)
     u0, s0, _ = run_fmm(f["x"], f["alpha"], f["sigma"], concurrent_far=0, **kw)
     assert np.array_equal(u1, u0) and np.array_equal(s1, s0)
+
+
+def test_fmm_fp32_random_positions_line_kernel_levels():
+    # uniform random positions on a depth-5 tree (2^21 - 77 particles: empty and crowded
+    # leaves, ragged counts, target chunks beyond 64 per leaf), BF16x3 on the source-line
+    # kernel, one near ring + ring-2 correction, concurrent far field
+    n_side = 128
+    h = 2 * np.pi / n_side
+    rng = np.random.default_rng(21)
+    N = 2 ** 21 - 77
+    x = rng.uniform(0, 2 * np.pi, (N, 3))
+    g = rng.normal(size=x.shape) * h ** 3
+    sigma = h
+    tid = wl.target_subset(N, 48, seed=6)
+    uo, so = oracle.direct(x, g, sigma, K=1, targets=tid)
+    u, s, info = run_fmm(x, g, sigma, p=10, depth=5, periodic_levels=0, m2l="bf16x3")
+    assert info["max_leaf"] > 64 and info["near_rings"] == 1 and info["correction_rings"] == 2
+    eu, es = rel_l2(u[tid], uo), rel_l2(s[tid], so)
+    print("random 2^21: max leaf %d, u %.3e S %.3e" % (info["max_leaf"], eu, es))
+    assert eu < 1e-4 and es < 1e-3
+
+
+@pytest.mark.parametrize("N", [1, 2, 65])
+def test_fmm_tiny_inputs(N):
+    # a handful of particles in a depth-2 tree (most leaves empty): the FMM still equals the
+    # direct sum over the same 27 image boxes
+    rng = np.random.default_rng(N)
+    x = rng.uniform(0, 2 * np.pi, (N, 3))
+    g = rng.normal(size=x.shape)
+    sigma = 0.3
+    uo, so = oracle.direct(x, g, sigma, K=1)
+    u, s, _ = run_fmm(x, g, sigma, p=10, depth=2, periodic_levels=0, m2l="bf16x3")
+    if N == 1:
+        # only the particle's own images: they cancel in pairs, u = S = 0; the FMM leaves its
+        # truncation error, measured against the field of the strength at one leaf width
+        w = 2 * np.pi / 4
+        gm = np.abs(g).max()
+        assert np.abs(u).max() < 1e-4 * gm / (4 * np.pi * w ** 2)
+        assert np.abs(s).max() < 1e-3 * gm ** 2 / (4 * np.pi * w ** 3)
+    else:
+        assert rel_l2(u, uo) < 1e-4 and rel_l2(s, so) < 1e-3
