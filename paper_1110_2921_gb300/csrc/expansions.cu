@@ -602,7 +602,10 @@ __device__ __forceinline__ typename C2<T>::type dcx(const typename C2<T>::type *
     return v;
 }
 
-template <typename T>
+#ifndef VFMM_L2P_PP
+#define VFMM_L2P_PP 2
+#endif
+template <typename T, int PP>
 __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__restrict__ xs,
                                                 const typename V4<T>::type *__restrict__ gs,
                                                 const int *__restrict__ ls, int nside, int log2n, T w, int p, int pc,
@@ -657,40 +660,65 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
     __syncthreads();
     const T zx = (cx + T(0.5)) * w, zy = (cy + T(0.5)) * w, zz = (cz + T(0.5)) * w;
     const T invw = T(1) / w;
-    for (int i = b0 + threadIdx.x; i < e0; i += blockDim.x) {
-        typename V4<T>::type xp = xs[i];
-        T x = (xp.x - zx) * invw, y = (xp.y - zy) * invw, z = (xp.z - zz) * invw;
-        T r2 = x * x + y * y + z * z;
-        T A[12];
+    // PP particles per thread: one table row load serves PP independent recursions
+    for (int i0 = b0 + threadIdx.x; i0 < e0; i0 += PP * blockDim.x) {
+        T x[PP], y[PP], z[PP], r2[PP];
+        T A[PP][12];
 #pragma unroll
-        for (int v = 0; v < 12; ++v) A[v] = 0;
-        T dre = 1, dim = 0;
+        for (int q = 0; q < PP; ++q) {
+            const int i = i0 + q * blockDim.x;
+            typename V4<T>::type xp = i < e0 ? xs[i] : make_v4<T>(zx, zy, zz, T(0));
+            x[q] = (xp.x - zx) * invw;
+            y[q] = (xp.y - zy) * invw;
+            z[q] = (xp.z - zz) * invw;
+            r2[q] = x[q] * x[q] + y[q] * y[q] + z[q] * z[q];
+#pragma unroll
+            for (int v = 0; v < 12; ++v) A[q][v] = 0;
+        }
+        T dre[PP], dim[PP];
+#pragma unroll
+        for (int q = 0; q < PP; ++q) {
+            dre[q] = 1;
+            dim[q] = 0;
+        }
         for (int m = 0; m < p; ++m) {
-            if (m > 0) {
-                T f = -inv2m_t<T>(m);
-                T nre = f * (x * dre - y * dim);
-                T nim = f * (x * dim + y * dre);
-                dre = nre;
-                dim = nim;
+            T pre[PP], pim[PP], ppre[PP], ppim[PP];
+#pragma unroll
+            for (int q = 0; q < PP; ++q) {
+                if (m > 0) {
+                    T f = -inv2m_t<T>(m);
+                    T nre = f * (x[q] * dre[q] - y[q] * dim[q]);
+                    T nim = f * (x[q] * dim[q] + y[q] * dre[q]);
+                    dre[q] = nre;
+                    dim[q] = nim;
+                }
+                pre[q] = dre[q];
+                pim[q] = dim[q];
+                ppre[q] = 0;
+                ppim[q] = 0;
             }
-            T pre = dre, pim = dim, ppre = 0, ppim = 0;
             const T wgt = m > 0 ? T(2) : T(1);  // the pair +-m of sum conj(Y) T
             int ci = cix(m, m);
             for (int n = m; n < p; ++n) {
-                T cre, cim;
-                if (n == m) {
-                    cre = dre;
-                    cim = dim;
-                } else {
-                    T c1 = T(2 * n - 1) * z, f = rec_t<T>(n, m);
-                    cre = (c1 * pre - r2 * ppre) * f;
-                    cim = (c1 * pim - r2 * ppim) * f;
-                    ppre = pre;
-                    ppim = pim;
-                    pre = cre;
-                    pim = cim;
+                T wre[PP], wim[PP];
+#pragma unroll
+                for (int q = 0; q < PP; ++q) {
+                    T cre, cim;
+                    if (n == m) {
+                        cre = dre[q];
+                        cim = dim[q];
+                    } else {
+                        T c1 = T(2 * n - 1) * z[q], f = rec_t<T>(n, m);
+                        cre = (c1 * pre[q] - r2[q] * ppre[q]) * f;
+                        cim = (c1 * pim[q] - r2[q] * ppim[q]) * f;
+                        ppre[q] = pre[q];
+                        ppim[q] = pim[q];
+                        pre[q] = cre;
+                        pim[q] = cim;
+                    }
+                    wre[q] = wgt * cre;
+                    wim[q] = wgt * cim;
                 }
-                const T wre = wgt * cre, wim = wgt * cim;
                 const T2 *row = W + ci * 12;
                 if constexpr (sizeof(T) == 4) {
                     // rows are 96 B and W starts 48 ncx bytes in: 16-byte loads of two entries
@@ -699,14 +727,18 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
 #pragma unroll
                     for (int v2 = 0; v2 < 6; ++v2) {
                         if (v2 < nv) {
-                            float4 q = r4[v2];
-                            A[2 * v2] += wre * q.x + wim * q.y;
-                            A[2 * v2 + 1] += wre * q.z + wim * q.w;
+                            float4 t = r4[v2];
+#pragma unroll
+                            for (int q = 0; q < PP; ++q) {
+                                A[q][2 * v2] += wre[q] * t.x + wim[q] * t.y;
+                                A[q][2 * v2 + 1] += wre[q] * t.z + wim[q] * t.w;
+                            }
                         }
                     }
                     if (nv == 1) {
                         T2 t = row[2];
-                        A[2] += wre * t.x + wim * t.y;
+#pragma unroll
+                        for (int q = 0; q < PP; ++q) A[q][2] += wre[q] * t.x + wim[q] * t.y;
                     }
                 } else {
                     const int nv = n < p - 1 ? 12 : 3;
@@ -714,7 +746,8 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
                     for (int v = 0; v < 12; ++v) {
                         if (v < nv) {
                             T2 t = row[v];
-                            A[v] += wre * t.x + wim * t.y;
+#pragma unroll
+                            for (int q = 0; q < PP; ++q) A[q][v] += wre[q] * t.x + wim[q] * t.y;
                         }
                     }
                 }
@@ -724,20 +757,25 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
         // psi_c = (1/4pi)(1/w) sum conj(Y) s F; d/dx = (1/w) d/dy
         const T s1 = T(0.0795774715459476679) * invw * invw;
         const T s2 = s1 * invw;
-        ufar[3 * (int64_t)i + 0] = s1 * A[0];
-        ufar[3 * (int64_t)i + 1] = s1 * A[1];
-        ufar[3 * (int64_t)i + 2] = s1 * A[2];
-        if (sfar) {  // S_a = gamma_k du_a/dx_k
-            typename V4<T>::type gp = gs[i];
-            sfar[3 * (int64_t)i + 0] = s2 * (gp.x * A[3] + gp.y * A[6] + gp.z * A[9]);
-            sfar[3 * (int64_t)i + 1] = s2 * (gp.x * A[4] + gp.y * A[7] + gp.z * A[10]);
-            sfar[3 * (int64_t)i + 2] = s2 * (gp.x * A[5] + gp.y * A[8] + gp.z * A[11]);
-        }
-        if (gfar) {  // velocity gradient du_a/dx_k at 3a + k
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+        for (int q = 0; q < PP; ++q) {
+            const int i = i0 + q * blockDim.x;
+            if (i >= e0) continue;
+            ufar[3 * (int64_t)i + 0] = s1 * A[q][0];
+            ufar[3 * (int64_t)i + 1] = s1 * A[q][1];
+            ufar[3 * (int64_t)i + 2] = s1 * A[q][2];
+            if (sfar) {  // S_a = gamma_k du_a/dx_k
+                typename V4<T>::type gp = gs[i];
+                sfar[3 * (int64_t)i + 0] = s2 * (gp.x * A[q][3] + gp.y * A[q][6] + gp.z * A[q][9]);
+                sfar[3 * (int64_t)i + 1] = s2 * (gp.x * A[q][4] + gp.y * A[q][7] + gp.z * A[q][10]);
+                sfar[3 * (int64_t)i + 2] = s2 * (gp.x * A[q][5] + gp.y * A[q][8] + gp.z * A[q][11]);
+            }
+            if (gfar) {  // velocity gradient du_a/dx_k at 3a + k
 #pragma unroll
-                for (int kk = 0; kk < 3; ++kk) gfar[9 * (int64_t)i + 3 * a + kk] = s2 * A[3 + 3 * kk + a];
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk) gfar[9 * (int64_t)i + 3 * a + kk] = s2 * A[q][3 + 3 * kk + a];
+            }
         }
     }
 }
@@ -750,12 +788,12 @@ int launch_l2p(Ctx *c, bool grad)
     const int ncx = (c->p + 1) * (c->p + 2) / 2;
     size_t sm = (size_t)(3 + 3 + 12) * ncx * 2 * c->esz;
     if (c->f64)
-        k_l2p<double><<<(unsigned)c->nleaf, L2P_BS, sm, c->stream>>>(
+        k_l2p<double, 1><<<(unsigned)c->nleaf, L2P_BS, sm, c->stream>>>(
             (const dvec4 *)c->xs.p, (const dvec4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,
             c->leaf_w, c->p, c->pc, (const double *)c->lexp.p + off, (double *)c->ufar.p,
             grad ? nullptr : (double *)c->sfar.p, grad ? (double *)c->gfar.p : nullptr);
     else
-        k_l2p<float><<<(unsigned)c->nleaf, L2P_BS, sm, c->stream>>>(
+        k_l2p<float, VFMM_L2P_PP><<<(unsigned)c->nleaf, L2P_BS / VFMM_L2P_PP, sm, c->stream>>>(
             (const float4 *)c->xs.p, (const float4 *)c->gs.p, (const int *)c->leaf_start.p, c->nside, log2n,
             (float)c->leaf_w, c->p, c->pc, (const float *)c->lexp.p + off, (float *)c->ufar.p,
             grad ? nullptr : (float *)c->sfar.p, grad ? (float *)c->gfar.p : nullptr);
