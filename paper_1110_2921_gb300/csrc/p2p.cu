@@ -7,18 +7,28 @@
 //   K = q(rho)/(4 pi r^3),  F = K'(r)/r,  q from Eq. (cutoff).
 // The near field is "solved exactly" (Section 3.1): the full smoothed kernel, no expansion.
 //
-// Design: one block per target leaf (and target chunk); each thread owns one target and
-// keeps nine FP32 accumulators (u, A = sum K gamma_j, B = sum F (gamma_i.r) gamma_j x r,
-// S = A x gamma_i + B); sources of one neighbour leaf are staged in shared memory and read
-// as warp-wide broadcasts.  The image shift is applied once per neighbour leaf to the
-// target position.  FP32 math:
-//   * 1/r from rsqrt, exp(-rho^2/2) from ex2, both single MUFU instructions;
+// FP32 kernel (k_p2p_f32): one warp per target leaf (and 64-target chunk), two targets per
+// lane.  The sources of each neighbour leaf are staged in shared memory as (x, gamma,
+// gamma x x) records relative to the target leaf centre (the image shift applied once per
+// leaf) and read as warp-wide broadcasts.  Per target four accumulated vectors,
+//   A = sum K gamma_j,  U = sum K (gamma_j x x_j),  D = sum f gamma_j,  E = sum f (gamma_j x x_j),
+// f = F (gamma_i . r), give u = A x x_i - U and S = A x gamma_i + D x x_i - E without a cross
+// product per pair.  The inner loop is chosen per run of source octants by the gap between
+// the target leaf's box and the octant's box: smoothed with the small-rho series branch,
+// smoothed, singular (gap >= 6.5 sigma), or, in ring 2 beyond the near ring, smoothed minus
+// singular for octants within rho_cut sigma (the Gaussian tail the far field lacks).
+// FP32 math:
+//   * 1/r from rsqrt, exp(-rho^2/2) from ex2 on coordinates pre-scaled by
+//     sqrt(log2 e / (2 sigma^2)), both single MUFU instructions;
 //   * erf(rho/sqrt2) by Abramowitz & Stegun 7.1.26 (Hastings' rational approximation,
 //     |error| <= 1.5e-7), which needs exactly the exp(-rho^2/2) already computed;
 //   * for rho < 0.5 the Taylor series of q/rho^3 and of K'/r in rho^2, which avoids the
 //     cancellation of q ~ rho^3 and the 1/r^5 of F, and gives the exact self-pair limit
 //     (K finite, r = 0 so every self term vanishes).
-// The epilogue adds the far field computed by L2P and scatters u, S to caller order.
+// The epilogue scatters u, S to caller order, adding the far field when it is given (in line);
+// with the concurrent far field, k_add_far adds it afterwards.  k_p2p_f64 (FP64 near field),
+// k_p2p_grad (velocity gradient for the adjoint) and the allocation-free direct sum at the end
+// of the file use one thread per target.
 #include "common.cuh"
 #include "vfmm_internal.h"
 
