@@ -11,13 +11,21 @@
 // hi*hi + hi*lo + lo*hi are accumulated in FP32 in TMEM; the dropped lo*lo term is ~2^-16
 // (BF16) or ~2^-22 (TF32) relative.
 //
-// Mechanics (sm_103a): 128 threads; one elected thread issues tcgen05.mma (M = 128,
-// N = 192, K = 16 bf16 / 8 tf32 per instruction) from shared-memory descriptors in the
-// canonical no-swizzle K-major layout (8-row x 16-byte core matrices; K-adjacent core
-// matrices 128 B apart, 8-row groups TC_KG x 128 B apart); operands stream through a
-// multi-stage pipeline; tcgen05.commit arrives on one mbarrier per stage so a stage is refilled
-// only after the MMAs that read it completed.  Every mbarrier wait is bounded: on timeout
-// the kernel sets an error bit, waits (bounded) for its own loads, frees TMEM and returns.
+// Two kernels share the operators and the pipeline mechanics:
+//   * k_m2l_lines (levels with 16 to 64 cells per side and parity, i.e. the large levels):
+//     128 target cells (whole z-lines) per CTA, offsets grouped by source line, one gathered
+//     source line serving all z shifts of its class (see the section below);
+//   * k_m2l_tc (levels 3 and 4): 64 target cells per CTA, the B tile of every offset gathered
+//     row by row, the offset list split over several CTAs when the level has few cells.
+//
+// Mechanics (sm_103a): one elected thread of warp 0 issues tcgen05.mma (M = 128, N = 192,
+// K = 16 bf16 / 8 tf32 per instruction) from shared-memory descriptors in the canonical
+// no-swizzle K-major layout (8-row x 16-byte core matrices); producer warps gather the source
+// rows with cp.async and one producer thread moves the pre-tiled translation matrices with
+// TMA bulk copies (expect_tx); tcgen05.commit arrives on one mbarrier per stage so a stage is
+// refilled only after the MMAs that read it completed.  Every mbarrier wait is bounded: on
+// timeout the kernel sets an error bit, waits (bounded) for its own loads, frees TMEM and
+// returns.
 #include "common.cuh"
 #include "vfmm_internal.h"
 
