@@ -31,9 +31,17 @@ __global__ void k_keys(int64_t n, const TIn *__restrict__ x, int nside, double L
         key = (c[0] * nside + c[1]) * nside + c[2];
         keys[i] = key;
     }
-    // one atomic per distinct leaf in the warp (neighbouring particles share leaves)
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    if (active && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[key], __popc(peers));
+    // one atomic per run of equal keys in the warp (neighbouring particles share leaves):
+    // the first lane of a run adds the run length
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    if (active && head) {
+        const unsigned later = heads & ~((2u << lane) - 1u);  // heads after this lane
+        const int next = later ? __ffs(later) - 1 : 32;
+        atomicAdd(&counts[key], next - lane);
+    }
 }
 
 // Exclusive scan, level 1: each block scans 1024 counts, writes local prefix and its total.
