@@ -89,7 +89,7 @@ int launch_gather_gamma(Ctx *c, const void *gamma)
 // P2M (Eq. fmm3dm): Mh_n^m = s_nm sum_j gamma_j Y_n^m((x_j - z)/w) for each leaf.
 // One block of 128 threads per leaf.  Phase 1: the harmonics of a chunk of particles go to
 // shared memory; each particle's orders m are split over P2M_BS / TP threads (the short
-// diagonal recurrence is repeated by each).  Phase 2: thread j owns coefficient j of all three
+// diagonal recurrence is repeated by each).  Phase 2: thread (h, j) owns coefficients j and j + 64 of all three
 // components and sums gamma_j Y over the chunk (conflict-free rows, broadcast strengths).
 template <typename T> struct P2MCfg {
     static constexpr int TP = sizeof(T) == 4 ? 64 : 32;  // particles per chunk
@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(const typename V4<T>::type *__re
     const int b = ls[leaf], e = ls[leaf + 1];
     const int nc = (p + 1) * (p + 1);
     const int q = threadIdx.x % TP, part = threadIdx.x / TP;
-    const int j = threadIdx.x;  // phase-2 coefficient
-    T a0 = 0, a1 = 0, a2 = 0;
+    const int jp = threadIdx.x & 63, half = threadIdx.x >> 6;  // phase 2: coefficient pair, particle parity
+    T a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
     for (int s0 = b; s0 < e; s0 += TP) {
         const int cnt = min(TP, e - s0);
         if (q < cnt) {
@@ -157,23 +157,44 @@ __global__ void __launch_bounds__(P2M_BS) k_p2m(const typename V4<T>::type *__re
             }
         }
         __syncthreads();
-        if (j < pc) {
-#pragma unroll 8
-            for (int t = 0; t < cnt; ++t) {
-                typename V4<T>::type gv = gsm[t];
-                T yv = Ysm[t * ys + j];
-                a0 += gv.x * yv;
-                a1 += gv.y * yv;
-                a2 += gv.z * yv;
-            }
+        // thread (half, jp) sums coefficients jp and jp + 64 over the particles of its parity:
+        // one broadcast strength load serves two coefficients
+#pragma unroll 4
+        for (int t = half; t < cnt; t += 2) {
+            typename V4<T>::type gv = gsm[t];
+            T y0 = Ysm[t * ys + jp], y1 = jp + 64 < pc ? Ysm[t * ys + jp + 64] : T(0);
+            a0 += gv.x * y0;
+            a1 += gv.y * y0;
+            a2 += gv.z * y0;
+            b0 += gv.x * y1;
+            b1 += gv.y * y1;
+            b2 += gv.z * y1;
         }
         __syncthreads();
     }
-    if (j < pc) {
+    // the two particle parities meet in shared memory (the harmonic table is free now)
+    T *red = Ysm;  // [64][6]
+    if (half == 1) {
+        red[6 * jp + 0] = a0;
+        red[6 * jp + 1] = a1;
+        red[6 * jp + 2] = a2;
+        red[6 * jp + 3] = b0;
+        red[6 * jp + 4] = b1;
+        red[6 * jp + 5] = b2;
+    }
+    __syncthreads();
+    if (half == 0) {
         T *out = M + (size_t)leaf * 3 * pc;
-        out[j] = a0;
-        out[pc + j] = a1;
-        out[2 * pc + j] = a2;
+        if (jp < pc) {
+            out[jp] = a0 + red[6 * jp + 0];
+            out[pc + jp] = a1 + red[6 * jp + 1];
+            out[2 * pc + jp] = a2 + red[6 * jp + 2];
+        }
+        if (jp + 64 < pc) {
+            out[jp + 64] = b0 + red[6 * jp + 3];
+            out[pc + jp + 64] = b1 + red[6 * jp + 4];
+            out[2 * pc + jp + 64] = b2 + red[6 * jp + 5];
+        }
     }
 }
 
