@@ -207,16 +207,16 @@ def profiled_traffic(kernel, src):
     return d.get("dram_bytes_per_launch")
 
 
-def oracle_rate(f, targets, K):
+def oracle_rate(f, targets, K, nthreads=0):
     """FP64 oracle (as it stands) on a target sample: seconds and threads used."""
     import oracle
     t0 = time.perf_counter()
-    oracle.direct(f["x"], f["alpha"], f["sigma"], K=K, targets=targets)
+    oracle.direct(f["x"], f["alpha"], f["sigma"], K=K, targets=targets, nthreads=nthreads)
     dt = time.perf_counter() - t0
-    return dt, os.cpu_count()
+    return dt, nthreads if nthreads > 0 else os.cpu_count()
 
 
-def cpu_baseline(f, ntargets):
+def cpu_baseline(f, ntargets, single_core=True):
     """Oracle particles/s for the workload's definition (27^3 image boxes), from a timed
     sample of targets with the central 27 boxes; the 27^3-box cost is the same loop over
     729 times as many (target, source, box) triples."""
@@ -229,8 +229,13 @@ def cpu_baseline(f, ntargets):
     value = ntargets / dt * 27.0 / boxes_full
     sample = ("%d targets of the %d-particle field, direct FP64 sum over the central 27 image boxes in %.1f s; "
               "scaled by 27/%d to the 27^3-box sum" % (ntargets, N, dt, boxes_full))
-    return {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle", "sample": sample,
-            "seconds": dt}
+    out = {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle", "sample": sample,
+           "seconds": dt}
+    if single_core:  # the same loop on one core, one target
+        dt1, _ = oracle_rate(f, tid[:1], K=1, nthreads=1)
+        out["single_core"] = {"value": 1.0 / dt1 * 27.0 / boxes_full, "cores": 1, "seconds": dt1,
+                              "sample": "1 target, central 27 boxes, scaled by 27/%d" % boxes_full}
+    return out
 
 
 def run_reference(args):
@@ -242,10 +247,10 @@ def run_reference(args):
     f = wl.make_vortex_lattice(n, args.k0, 1)
     nt = args.cpu_targets or os.cpu_count()
     for _ in range(args.warmup):
-        cpu_baseline(f, nt)
+        cpu_baseline(f, nt, single_core=False)
     vals, secs = [], 0.0
     for _ in range(args.steps):
-        cb = cpu_baseline(f, nt)
+        cb = cpu_baseline(f, nt, single_core=False)
         vals.append(cb["value"])
         secs += cb["seconds"]
     value = len(vals) * nt / secs * 27.0 / (27 ** 3)
