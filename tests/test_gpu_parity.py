@@ -150,6 +150,22 @@ def test_errors_reported():
         with pytest.raises(vf.VfmmError) as e:
             h.eval(g, float("nan"))
         assert e.value.status == -1
+        # a core so wide that rho_cut sigma exceeds two leaf widths: the near field would need
+        # a third ring
+        xx = torch.rand(4096, 3, device="cuda") * 6.28
+        gg = torch.zeros(4096, 3, device="cuda")
+        h2 = vf.VortexFMM(m2l="fp32", depth=3)
+        try:
+            h2.build_tree(xx)
+            with pytest.raises(vf.VfmmError) as e:
+                h2.eval(gg, 1.0)
+            assert e.value.status == -7
+            # the spectrum wants a power-of-two lattice
+            with pytest.raises(vf.VfmmError) as e:
+                h2.energy_spectrum(torch.zeros(12 ** 3, 3, device="cuda"), 12, 4)
+            assert e.value.status == -7
+        finally:
+            h2.close()
     finally:
         h.close()
 
