@@ -751,10 +751,21 @@ int vfmm_eval_host(vfmm_handle h, int64_t n, const void *x, const void *gamma, d
     if ((st = ensure(c, c->hg, bytes, "host staging gamma"))) return st;
     if ((st = ensure(c, c->hu, bytes, "host staging u"))) return st;
     if ((st = ensure(c, c->hs, bytes, "host staging S"))) return st;
+    // x on the caller's stream (the tree needs it first); gamma on the side stream, so its copy
+    // runs while the tree is built, joined before the evaluation
     cudaError_t e = cudaMemcpyAsync(c->hx.p, x, bytes, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->hg.p, gamma, bytes, cudaMemcpyHostToDevice, c->stream);
+    const bool side_copy = c->side != nullptr;
+    if (e == cudaSuccess && side_copy) {
+        cudaEventRecord(c->ev[11], c->stream);  // the side stream follows earlier work on the caller's
+        cudaStreamWaitEvent(c->side, c->ev[11], 0);
+        e = cudaMemcpyAsync(c->hg.p, gamma, bytes, cudaMemcpyHostToDevice, c->side);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev[10], c->side);
+    } else if (e == cudaSuccess) {
+        e = cudaMemcpyAsync(c->hg.p, gamma, bytes, cudaMemcpyHostToDevice, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "host to device copy");
     if ((st = build_impl(c, n, c->hx.p))) return st;
+    if (side_copy) cudaStreamWaitEvent(c->stream, c->ev[10], 0);
     if ((st = eval_impl(c, c->hg.p, sigma, c->hu.p, s_out ? c->hs.p : nullptr))) return st;
     e = cudaMemcpyAsync(u_out, c->hu.p, bytes, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && s_out) e = cudaMemcpyAsync(s_out, c->hs.p, bytes, cudaMemcpyDeviceToHost, c->stream);

@@ -244,3 +244,21 @@ def test_fmm_tiny_inputs(N):
         assert np.abs(s).max() < 1e-3 * gm ** 2 / (4 * np.pi * w ** 3)
     else:
         assert rel_l2(u, uo) < 1e-4 and rel_l2(s, so) < 1e-3
+
+
+def test_eval_host_matches_device_path():
+    # the host-memory entry point (copies in, tree, evaluation, copies out) gives the device
+    # path's results, twice in a row with new positions (the strength copy overlaps the tree)
+    torch = pytest.importorskip("torch")
+    import paper_1110_2921_gb300 as vf
+    f = wl.make_vortex_lattice(32, 4, 1)
+    for it, x in enumerate((f["x"], wl.jitter(f["x"], f["h"], 0.3, seed=4))):
+        u_dev, s_dev, _ = run_fmm(x, f["alpha"], f["sigma"], p=10, periodic_levels=2, m2l="bf16x3")
+        h = vf.VortexFMM(p=10, periodic_levels=2, m2l="bf16x3")
+        try:
+            xh = torch.tensor(x, dtype=torch.float32).pin_memory()
+            gh = torch.tensor(f["alpha"], dtype=torch.float32).pin_memory()
+            u, s = h.eval_host(xh.numpy(), gh.numpy(), f["sigma"])
+        finally:
+            h.close()
+        assert np.array_equal(u.astype(np.float64), u_dev) and np.array_equal(s.astype(np.float64), s_dev)
