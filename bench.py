@@ -195,8 +195,10 @@ def source_hash(*names):
     return h.hexdigest()[:12]
 
 
-def profiled_traffic(kernel, src):
-    """DRAM bytes per launch from a committed ncu capture, if the kernel source is unchanged."""
+def profiled_traffic(kernel, src, n_particles):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel source is unchanged,
+    scaled from the captured case to n_particles (the kernel reads each sorted particle and
+    writes each output once, so its traffic is proportional to the particle count)."""
     path = os.path.join(ROOT, "profiles", "counters.json")
     try:
         d = json.load(open(path))[kernel]
@@ -204,7 +206,10 @@ def profiled_traffic(kernel, src):
         return None
     if d.get("source_hash") != source_hash(*src):
         return None
-    return d.get("dram_bytes_per_launch")
+    measured, n_meas = d.get("measured_bytes"), d.get("measured_particles")
+    if measured is None or not n_meas:
+        return d.get("dram_bytes_per_launch")
+    return measured * n_particles / n_meas
 
 
 def oracle_rate(f, targets, K, nthreads=0):
@@ -432,7 +437,7 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peak = 2 * 128 * sms * 2.070e9 / 1e12
-    traffic = profiled_traffic("k_p2p_f32", ["p2p.cu"])
+    traffic = profiled_traffic("k_p2p_f32", ["p2p.cu"], N)
     phases = {k: round(statistics.mean(p[k] for p in phase_ms), 3) for k in phase_ms[0]}
 
     # the tensor-core M2L: algorithmic flops of the 121 x 121 translations (three split
@@ -484,7 +489,7 @@ def main():
                    % (n, N, args.k0, args.p), "n_particles": N, "p": args.p, "m2l": args.m2l,
                    "periodic_levels": args.periodic_levels, "depth": info["depth"], "near_rings": R,
                    "correction_rings": Rc, "rho_cut": args.rho_cut,
-                   "l2": "inputs (x, gamma 402 MB) larger than L2; no flush",
+                   "l2": "inputs (x, gamma %d MB) larger than L2 (129 MB); no flush" % (2 * N * 3 * 4 // 2 ** 20),
                    "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
