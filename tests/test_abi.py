@@ -41,6 +41,9 @@ def test_host_only_calls():
     assert nv.lib().vfmm_create(ctypes.byref(bad), ctypes.byref(h)) == nv.VFMM_ERR_ARG
     assert nv.lib().vfmm_build_tree(None, 10, None) == nv.VFMM_ERR_ARG
     assert nv.lib().vfmm_sync(None) == nv.VFMM_ERR_ARG
+    assert nv.lib().vfmm_energy_spectrum(None, 16, None, 8, None) == nv.VFMM_ERR_ARG
+    assert nv.lib().vfmm_derivative_moments(None, 10, None, None) == nv.VFMM_ERR_ARG
+    assert cfg.concurrent_far == 1 and abs(cfg.rho_cut - 5.0) < 1e-15
 
 
 def test_layout_matches_header():
