@@ -489,7 +489,7 @@ def main():
                    % (n, N, args.k0, args.p), "n_particles": N, "p": args.p, "m2l": args.m2l,
                    "periodic_levels": args.periodic_levels, "depth": info["depth"], "near_rings": R,
                    "correction_rings": Rc, "rho_cut": args.rho_cut,
-                   "l2": "inputs (x, gamma %d MB) larger than L2 (129 MB); no flush" % (2 * N * 3 * 4 // 2 ** 20),
+                   "l2": "inputs (x, gamma %d MiB) larger than L2 (129 MB); no flush" % (2 * N * 3 * 4 // 2 ** 20),
                    "parallelism": "replicas" if ws > 1 else "single"},
         "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
