@@ -1,5 +1,8 @@
 // C-ABI of libvfmm: handle management, tree build and the evaluation pipeline
 // P2M -> M2M -> (FP64 root + periodic lattice operator) -> M2L -> L2L -> L2P -> P2P.
+// In the FP32 velocity/stretching evaluation the far-field chain (P2M ... L2P) runs on a
+// handle-owned high-priority stream beside the P2P on the caller's stream, and a last kernel
+// scatters the far field onto the outputs once both are done.
 #include "common.cuh"
 #include "vfmm_internal.h"
 

@@ -1,5 +1,6 @@
 // Expansion kernels of the periodic FMM: P2M, the gathered-column GEMM that performs M2M,
-// M2L and L2L on the CUDA cores, the FP64 root / periodic lattice step, and L2P.
+// M2L and L2L on the CUDA cores (split over k-blocks on small levels), the FP64 root /
+// periodic lattice step, L2P, and the scatter that adds the far field to the outputs.
 //
 // Section 3.1: the vector potential psi_c = sum_j gamma_{j,c} G (three scalar Laplace
 // potentials) is expanded in multipoles (Eq. fmm3dm) and locals (Eq. fmm3dl); velocity is
