@@ -217,11 +217,9 @@ __device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, fl
     a.E2 = fmaf(f, cj.z, a.E2);
 }
 
-// Tuning: P3_SPLIT groups of lanes hold the same P3_TPT targets each and split the sources
-// between them (partial sums combined by shuffles at the end).
-#ifndef VFMM_P3_SPLIT
-#define VFMM_P3_SPLIT 1
-#endif
+// Tuning knobs (compile-time): targets per lane and the unroll of the source loop.  Measured
+// alternatives (four targets per lane with the two half-warps splitting the sources, other
+// unrolls and occupancies) were slower or equal.
 #ifndef VFMM_P3_TPT
 #define VFMM_P3_TPT 2
 #endif
@@ -229,13 +227,10 @@ __device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, fl
 #define VFMM_P3_UNROLL 2
 #endif
 constexpr int P3_THREADS = 32;   // one warp per target leaf chunk
-constexpr int P3_SPLIT = VFMM_P3_SPLIT;
-constexpr int P3_GROUP = P3_THREADS / P3_SPLIT;  // lanes per source group
-constexpr int P3_TPT = VFMM_P3_TPT;              // targets per thread
-constexpr int P3_TARGETS = P3_GROUP * P3_TPT;    // targets per block
+constexpr int P3_TPT = VFMM_P3_TPT;              // targets per lane
+constexpr int P3_TARGETS = P3_THREADS * P3_TPT;  // targets per block
 constexpr int P3_TILE = 64;      // staged sources
 constexpr int P3_UNROLL = VFMM_P3_UNROLL;
-static_assert(P3_SPLIT == 1 || P3_SPLIT == 2, "one or two source groups");
 
 // one staged source: scaled position relative to the target leaf centre, strength, and
 // c = gamma x x (the cross product the velocity sum needs, formed once per source)
@@ -247,23 +242,12 @@ template <int MODE>
 __device__ __forceinline__ void tile3(const P3Const &k, const float (&xi)[P3_TPT][3], const float (&gi)[P3_TPT][3],
                                       const Src3 *src, int j0, int j1, Acc3 (&acc)[P3_TPT])
 {
-    // source group h takes the sources j0 + h, j0 + h + P3_SPLIT, ...
-    const int h = P3_SPLIT == 1 ? 0 : (int)(threadIdx.x / P3_GROUP);
 #pragma unroll P3_UNROLL
-    for (int j = j0 + h; j < j1; j += P3_SPLIT) {
+    for (int j = j0; j < j1; ++j) {
         const float4 xj = src[j].x, gj = src[j].g, cj = src[j].c;
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) pair3<MODE>(k, xi[q][0], xi[q][1], xi[q][2], gi[q][0], gi[q][1], gi[q][2], xj, gj, cj, acc[q]);
     }
-}
-
-// sum of the source groups' partial sums (every group ends with the total)
-__device__ __forceinline__ void reduce_groups(Acc3 &a)
-{
-    if (P3_SPLIT == 1) return;
-    float *v = reinterpret_cast<float *>(&a);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], P3_GROUP);
 }
 
 struct AccD {
@@ -359,13 +343,12 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
     const float zx = (cx + 0.5f) * leaf_w, zy = (cy + 0.5f) * leaf_w, zz = (cz + 0.5f) * leaf_w;
     const float s = kc.s;
     const float4 tlo = bbox[2 * leaf], thi = bbox[2 * leaf + 1];
-    const int hl = threadIdx.x % P3_GROUP, grp = threadIdx.x / P3_GROUP;
     for (int t0 = tb + blockIdx.y * P3_TARGETS; t0 < te; t0 += gridDim.y * P3_TARGETS) {
         float xi[P3_TPT][3], gi[P3_TPT][3];
         int tix[P3_TPT];
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) {
-            int ti = t0 + hl + q * P3_GROUP;
+            int ti = t0 + threadIdx.x + q * P3_THREADS;
             tix[q] = ti;
             float4 x = ti < te ? xs[ti] : make_float4(zx, zy, zz, 0.f);
             float4 g = ti < te ? gs[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -457,15 +440,12 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
                         }
                     }
                 }
-        // u = s^2 (A x x^ - U), S = s^3 (A x gamma + D x x^ - E), times 1/(4 pi); source group
-        // h writes its share of the targets
+        // u = s^2 (A x x^ - U), S = s^3 (A x gamma + D x x^ - E), times 1/(4 pi)
         const float su = INV_4PI_F * s * s, ss = su * s;
-#pragma unroll
-        for (int q = 0; q < P3_TPT; ++q) reduce_groups(acc[q]);
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) {
             int ti = tix[q];
-            if (ti >= te || (q * P3_SPLIT) / P3_TPT != grp) continue;
+            if (ti >= te) continue;
             const Acc3 &a = acc[q];
             const float *x = xi[q], *g = gi[q];
             float u0 = su * (a.A1 * x[2] - a.A2 * x[1] - a.U0);
