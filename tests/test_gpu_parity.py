@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
 
-Tolerances (derived in the design notes):
+Tolerances (each follows from the arithmetic it bounds):
 * direct sum, FP64 kernels: 1e-12 relative L2 (only summation order and erf/exp rounding
   differ);
 * direct sum, FP32 kernels: 2e-5 (FP32 accumulation of ~1e5 terms plus the 1.5e-7 error of

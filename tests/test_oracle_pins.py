@@ -133,6 +133,57 @@ def test_bruteforce_mpmath_small():
     assert np.allclose(S, Sm, rtol=1e-11, atol=1e-13 * np.abs(Sm).max())
 
 
+def _cluster(sigma, seed):
+    """Six sources whose pair distances fall between 0.05 sigma and 0.45 sigma (the series
+    branch of K and F, rho < 0.5), with random strengths."""
+    rng = np.random.default_rng(seed)
+    c = np.array([1.1, 2.3, 0.7])
+    d = rng.normal(size=(6, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    x = c + d * (np.array([0.0, 0.03, 0.08, 0.12, 0.17, 0.21])[:, None] * sigma)
+    g = rng.normal(size=(6, 3))
+    return x, g
+
+
+@pytest.mark.slow
+def test_bruteforce_mpmath_series_branch():
+    # the same 40-digit brute force on a cluster where every pair sits at rho < 0.5: the
+    # series of k = q/rho^3 and f = k'/rho (Eqs. cutoff, stretching) against quadrature and
+    # numerical differentiation in mpmath
+    sigma = 0.6
+    x, g = _cluster(sigma, 17)
+    tid = np.arange(6)
+    r = np.linalg.norm(x[:, None] - x[None], axis=2)[np.triu_indices(6, 1)] / sigma
+    assert 0.02 < r.min() and r.max() < 0.5
+    u, S = oracle.direct(x, g, sigma, K=0, targets=tid)
+    um, Sm = _mp_sum(x, g, x, g, tid, sigma, 2 * np.pi, 0)
+    assert np.allclose(u, um, rtol=1e-12, atol=1e-14 * np.abs(um).max())
+    assert np.allclose(S, Sm, rtol=1e-11, atol=1e-13 * np.abs(Sm).max())
+
+
+def test_gradient_series_branch_matches_fd():
+    # grad u at a point within 0.3 sigma of sources (rho < 0.5: F from its series) against
+    # central differences of u, whose K alone is pinned by the single-blob closed form; and
+    # S = (gamma_t . grad) u there (Eq. stretching)
+    sigma = 0.6
+    x, g = _cluster(sigma, 23)
+    xt = (x[0] + np.array([0.11, -0.07, 0.05]) * sigma)[None]
+    rho = np.linalg.norm(x - xt, axis=1) / sigma
+    assert rho.min() < 0.2 and (rho < 0.5).sum() >= 4
+    gt = np.array([[0.4, -0.9, 0.3]])
+    u, S, G = oracle.direct(x, g, sigma, K=0, xt=xt, gt=gt, grad=True)
+    eps = 1e-5 * sigma
+    J = np.zeros((3, 3))
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = eps
+        up, _ = oracle.direct(x, g, sigma, K=0, xt=xt + e)
+        um, _ = oracle.direct(x, g, sigma, K=0, xt=xt - e)
+        J[:, k] = (up[0] - um[0]) / (2 * eps)
+    assert np.allclose(G[0], J, rtol=1e-7, atol=1e-9 * np.abs(J).max()), (G[0], J)
+    assert np.allclose(S[0], J @ gt[0], rtol=1e-7, atol=1e-9 * np.abs(S).max())
+
+
 def test_stretching_equals_directional_derivative_of_u():
     # S_i = (gamma_i . grad) u at x_i, checked by central differences of the oracle's own u;
     # the displaced point lies on the line through x_i along gamma_i, where the self blob's

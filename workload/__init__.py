@@ -3,8 +3,8 @@
 This module holds no Biot-Savart or FMM arithmetic: it only builds the particle
 set (positions, strengths, core size) that both sides consume.
 
-Construction (Section 4.2, Eq. initspec of the paper, with the readings listed in
-the design notes):
+Construction (Section 4.2, Eq. initspec of the paper; where the paper is silent the
+readings are stated per item below):
 
 * particles sit at the centres of an n^3 lattice in [0, 2*pi)^3, x = (i + 1/2) h,
   h = 2*pi/n (the paper places vortex elements between spectral grid points);
