@@ -145,3 +145,91 @@ void oracle_direct(int64_t ns, const double *xs, const double *gs,
         if (G) for (int a = 0; a < 9; ++a) G[9 * i + a] = Gi[a];
     }
 }
+
+/*
+ * The same image-cube sum restricted to the image boxes kmin <= max|n_i| <= kmax with
+ * kmin >= 2, for the case where every such pair is at least 10 sigma apart
+ * ((kmin - 1) L >= 10 sigma for positions in [0, L)^3).  There q(rho) of Eq. (cutoff) is 1 in
+ * FP64 (1 - q(10) < 2e-21) and the Gaussian term of F is below 1e-19 of the 3q/r^5 term, so
+ * the definition reduces exactly (to FP64 rounding) to the singular Biot-Savart kernel
+ * K = 1/(4 pi r^3), F = -3 K / r^2.  This is the far-image increment of Section 4.1's
+ * 3^3 x 3^3 x 3^3 image cube beyond the central 27 boxes.  Targets xt, gt (nt x 3) are
+ * positions and strengths, none of them a source of the primary box (n = 0 is excluded).
+ * The work is split over image boxes; each thread sums its boxes into its own partial
+ * sums, which are added at the end.  u, S: nt x 3 outputs (overwritten).
+ * Returns 0, or -1 if the distance condition does not hold (nothing is computed).
+ */
+int oracle_far_images(int64_t ns, const double *xs, const double *gs,
+                      int64_t nt, const double *xt, const double *gt,
+                      double sigma, double L, int kmin, int kmax,
+                      double *u, double *S, int nthreads)
+{
+    if (kmin < 2 || kmax < kmin || (kmin - 1) * L < 10.0 * sigma) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    (void)nthreads;
+    const double c4pi = 1.0 / (4.0 * ORACLE_PI);
+    /* structure-of-arrays copies of the sources */
+    double *sx = (double *)malloc(sizeof(double) * 6 * (size_t)ns);
+    if (!sx) return -1;
+    double *sy = sx + ns, *sz = sy + ns, *ga = sz + ns, *gb = ga + ns, *gc = gb + ns;
+    for (int64_t j = 0; j < ns; ++j) {
+        sx[j] = xs[3 * j]; sy[j] = xs[3 * j + 1]; sz[j] = xs[3 * j + 2];
+        ga[j] = gs[3 * j]; gb[j] = gs[3 * j + 1]; gc[j] = gs[3 * j + 2];
+    }
+    /* the image boxes of the shell */
+    int side = 2 * kmax + 1;
+    int *boxes = (int *)malloc(sizeof(int) * 3 * (size_t)side * side * side);
+    if (!boxes) { free(sx); return -1; }
+    int nb = 0;
+    for (int nx = -kmax; nx <= kmax; ++nx)
+        for (int ny = -kmax; ny <= kmax; ++ny)
+            for (int nz = -kmax; nz <= kmax; ++nz) {
+                int m = abs(nx); if (abs(ny) > m) m = abs(ny); if (abs(nz) > m) m = abs(nz);
+                if (m < kmin) continue;
+                boxes[3 * nb] = nx; boxes[3 * nb + 1] = ny; boxes[3 * nb + 2] = nz;
+                ++nb;
+            }
+    for (int64_t i = 0; i < 3 * nt; ++i) { u[i] = 0.0; S[i] = 0.0; }
+#pragma omp parallel
+    {
+        double *acc = (double *)calloc(6 * (size_t)nt, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+        for (int b = 0; b < nb; ++b) {
+            const double shx = boxes[3 * b] * L, shy = boxes[3 * b + 1] * L, shz = boxes[3 * b + 2] * L;
+            for (int64_t i = 0; i < nt; ++i) {
+                /* r = x_i - (x_j + n L) */
+                const double tx = xt[3 * i] - shx, ty = xt[3 * i + 1] - shy, tz = xt[3 * i + 2] - shz;
+                const double t0 = gt[3 * i], t1 = gt[3 * i + 1], t2 = gt[3 * i + 2];
+                double u0 = 0, u1 = 0, u2 = 0, s0 = 0, s1 = 0, s2 = 0;
+#pragma omp simd reduction(+ : u0, u1, u2, s0, s1, s2)
+                for (int64_t j = 0; j < ns; ++j) {
+                    double r0 = tx - sx[j], r1 = ty - sy[j], r2 = tz - sz[j];
+                    double rr2 = r0 * r0 + r1 * r1 + r2 * r2;
+                    double rinv = 1.0 / sqrt(rr2);
+                    double K = rinv * rinv * rinv;
+                    double F = -3.0 * K * rinv * rinv;
+                    double w0 = gb[j] * r2 - gc[j] * r1, w1 = gc[j] * r0 - ga[j] * r2, w2 = ga[j] * r1 - gb[j] * r0;
+                    double fg = F * (t0 * r0 + t1 * r1 + t2 * r2);
+                    u0 += K * w0; u1 += K * w1; u2 += K * w2;
+                    s0 += K * (gb[j] * t2 - gc[j] * t1) + fg * w0;
+                    s1 += K * (gc[j] * t0 - ga[j] * t2) + fg * w1;
+                    s2 += K * (ga[j] * t1 - gb[j] * t0) + fg * w2;
+                }
+                acc[6 * i] += u0; acc[6 * i + 1] += u1; acc[6 * i + 2] += u2;
+                acc[6 * i + 3] += s0; acc[6 * i + 4] += s1; acc[6 * i + 5] += s2;
+            }
+        }
+#pragma omp critical
+        for (int64_t i = 0; i < nt; ++i)
+            for (int a = 0; a < 3; ++a) {
+                u[3 * i + a] += c4pi * acc[6 * i + a];
+                S[3 * i + a] += c4pi * acc[6 * i + 3 + a];
+            }
+        free(acc);
+    }
+    free(boxes);
+    free(sx);
+    return 0;
+}

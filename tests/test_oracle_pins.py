@@ -4,6 +4,7 @@ Each test targets one plausible mistake: a wrong normalisation of q (Eq. cutoff)
 wrong sign or operand order in the cross products (Eq. biotsavart), a dropped or
 mis-signed term in F (Eq. stretching), a wrong image lattice (Section 4.1).
 """
+import itertools
 import numpy as np
 import pytest
 from scipy import integrate
@@ -479,3 +480,48 @@ def test_derivative_moments_gaussian_samples():
     g = rng.standard_normal((1_000_000, 9))
     _, _, _, F3, F4 = oracle.diagnostics.derivative_moments(g)
     assert abs(F3) < 5 * np.sqrt(15.0 / 3e6) and abs(F4 - 3.0) < 5 * np.sqrt(96.0 / 3e6)
+
+
+def test_far_images_is_the_cube_sum_beyond_the_central_boxes():
+    # the far-image increment (image boxes 2 <= max|n| <= K, every pair >= 10 sigma apart) equals
+    # the full smoothed-kernel cube sum over the same boxes (Section 4.1 images; there q = 1 to
+    # FP64 rounding), and its S term is pinned by a 30-digit sum of the singular kernel
+    # K = 1/(4 pi r^3), F = K'(r)/r = -3/(4 pi r^5) written out independently here
+    rng = np.random.default_rng(17)
+    L = 2 * np.pi
+    xs = rng.uniform(0, L, (24, 3))
+    gs = rng.normal(size=(24, 3))
+    xt = rng.uniform(0, L, (3, 3))
+    gt = rng.normal(size=(3, 3))
+    sigma = 0.3
+    uf, Sf = oracle.far_images(xs, gs, xt, gt, sigma, L=L, kmin=2, K=3)
+    ud, Sd = oracle.direct(xs, gs, sigma, L=L, K=3, kmin=2, xt=xt, gt=gt)
+    assert np.allclose(uf, ud, rtol=1e-11, atol=1e-13 * np.abs(ud).max())
+    assert np.allclose(Sf, Sd, rtol=1e-11, atol=1e-13 * np.abs(Sd).max())
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    for i in range(len(xt)):
+        u = [mp.mpf(0)] * 3
+        S = [mp.mpf(0)] * 3
+        for n in itertools.product(range(-2, 3), repeat=3):
+            if max(abs(v) for v in n) < 2:
+                continue
+            for j in range(len(xs)):
+                r = [mp.mpf(xt[i][a]) - mp.mpf(xs[j][a]) - n[a] * mp.mpf(L) for a in range(3)]
+                rr = mp.sqrt(r[0] ** 2 + r[1] ** 2 + r[2] ** 2)
+                K = 1 / (4 * mp.pi * rr ** 3)
+                F = -3 / (4 * mp.pi * rr ** 5)
+                g = [mp.mpf(v) for v in gs[j]]
+                h = [mp.mpf(v) for v in gt[i]]
+                W = [g[1] * r[2] - g[2] * r[1], g[2] * r[0] - g[0] * r[2], g[0] * r[1] - g[1] * r[0]]
+                X = [g[1] * h[2] - g[2] * h[1], g[2] * h[0] - g[0] * h[2], g[0] * h[1] - g[1] * h[0]]
+                hr = h[0] * r[0] + h[1] * r[1] + h[2] * r[2]
+                for a in range(3):
+                    u[a] += K * W[a]
+                    S[a] += K * X[a] + F * hr * W[a]
+        u2, S2 = oracle.far_images(xs, gs, xt[i:i + 1], gt[i:i + 1], sigma, L=L, kmin=2, K=2)
+        assert np.allclose(u2[0], [float(v) for v in u], rtol=1e-12, atol=1e-15)
+        assert np.allclose(S2[0], [float(v) for v in S], rtol=1e-12, atol=1e-15)
+    # boxes closer than 10 sigma are refused (the reduction to the singular kernel would not hold)
+    with pytest.raises(ValueError):
+        oracle.far_images(xs, gs, xt, gt, L / 9.0, L=L, kmin=2, K=3)
