@@ -30,6 +30,9 @@ METRIC = "particles/s for u+stretching at 256³ (p=10), rel-L2 err vs FP64 direc
 PAPER_PARTICLES_PER_S = 0.84e6   # 256^3 / 20 s per step at p=10 on one C2070 (paper, Section 4.1)
 FLOPS_PER_PAIR = 61              # FP32 operations of one smoothed P2P pair (FMA = 2), + 3 MUFU
 FLOPS_PER_PAIR_SINGULAR = 42     # a pair of leaves >= 6.5 sigma apart (singular kernel), + 1 MUFU
+ALGO_FLOPS_PER_PAIR = 70         # algorithmic work of one pair of Eqs. (biotsavart)+(stretching) with the
+                                 # smoothed kernel: difference, r^2, K, F, two cross products, the
+                                 # projection gamma_i . r and six accumulations (FMA = 2)
 
 
 def parse():
@@ -49,6 +52,7 @@ def parse():
     ap.add_argument("--check", type=int, default=16, help="sampled targets for the oracle error (0 = off)")
     ap.add_argument("--cpu-targets", type=int, default=0, help="oracle targets for cpu_baseline (0 = one per host core)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--peaks", type=int, default=1, help="measure the FP32/MUFU/FP64/TF32/BF16 peaks (probe kernels)")
     ap.add_argument("--workload", default="eval", choices=["eval", "timestep"],
                     help="eval: u + S per step (the metric); timestep: ten Heun steps + one reinitialisation")
     return ap.parse_args()
@@ -187,6 +191,49 @@ def p2p_work(x, L, depth, R, sigma, Rc=0, rho_cut=6.0):
     return p_s + p_g, FLOPS_PER_PAIR * p_s + FLOPS_PER_PAIR_SINGULAR * p_g
 
 
+PROBE_REPS = {"fp32_ffma": 40000, "mufu_ex2": 5000, "mufu_rsqrt": 5000, "fp64_dfma": 600,
+              "tf32_tcgen05": 400000, "bf16_tcgen05": 400000}
+
+
+def measure_peaks(dev, stream, repeats=3):
+    """Peak rates of the units the path uses, from the library's probe kernels (one launch each,
+    CUDA events on the launching stream, best of ``repeats`` after one warm-up), with the SM
+    clock sampled while they run.  Units: TFLOP/s (FMA and MMA: 2 flops each), Gop/s (MUFU)."""
+    import torch
+    from paper_1110_2921_gb300 import _native as nv
+    kinds = {"fp32_ffma": nv.VFMM_PROBE_FFMA, "mufu_ex2": nv.VFMM_PROBE_EX2, "mufu_rsqrt": nv.VFMM_PROBE_RSQRT,
+             "fp64_dfma": nv.VFMM_PROBE_DFMA, "tf32_tcgen05": nv.VFMM_PROBE_MMA_TF32,
+             "bf16_tcgen05": nv.VFMM_PROBE_MMA_BF16}
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    sp = stream.cuda_stream
+    clocks = ClockSampler(dev.index)
+    out = {}
+    for name, kind in kinds.items():
+        reps = PROBE_REPS[name]
+        nv.vfmm_probe_peak(kind, reps // 10, sp, err.data_ptr())
+        best = None
+        for _ in range(repeats):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ops = nv.vfmm_probe_peak(kind, reps, sp, err.data_ptr())
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        scale = 1e9 if name.startswith("mufu") else 1e12
+        out[name] = ops / (best / 1e3) / scale
+        out[name + "_ms"] = best
+    clk = clocks.stop()
+    if int(err.item()) != 0:
+        raise RuntimeError("a tcgen05 probe reported a wait timeout")
+    out["units"] = "TFLOP/s (fp32, fp64, tf32, bf16), Gop/s (mufu)"
+    out["how"] = ("probe kernels of libvfmm (vfmm_probe_peak), one launch each timed with CUDA events, best of %d"
+                  % repeats)
+    out["clocks"] = clk
+    return out
+
+
 def source_hash(*names):
     h = hashlib.sha1()
     for nm in names:
@@ -210,6 +257,18 @@ def profiled_traffic(kernel, src, n_particles):
     if measured is None or not n_meas:
         return d.get("dram_bytes_per_launch")
     return measured * n_particles / n_meas
+
+
+def load_golden(n, k0):
+    """Stored oracle values at sampled targets of the 256^3, k0 = 4 benchmark field (written by
+    tests/golden/make_field256.py from the oracle), or None for other workloads."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", "field256_k4_seed1.txt")
+    if n != 256 or k0 != 4 or not os.path.exists(path):
+        return None
+    a = np.loadtxt(path)
+    return {"index": a[:, 0].astype(np.int64), "face": a[:, 1] > 0.5, "u_near": a[:, 2:5],
+            "S_near": a[:, 5:8], "u_far": a[:, 8:11], "S_far": a[:, 11:14]}
 
 
 def oracle_rate(f, targets, K, nthreads=0):
@@ -391,6 +450,12 @@ def main():
         torch.distributed.barrier()
     ms = t0.elapsed_time(t1)
     eval_ms = statistics.median(a.elapsed_time(b) for a, b in ev_pairs)
+    # outputs of the last timed step at the stored oracle targets (before other handles reuse U, S)
+    gold = load_golden(n, args.k0) if (args.check and rank == 0) else None
+    timed_out = None
+    if gold is not None:
+        idx = torch.tensor(gold["index"], dtype=torch.int64, device=dev)
+        timed_out = (U[idx].double().cpu().numpy(), S[idx].double().cpu().numpy())
     clk = clocks.stop() if clocks else None
     ms_max, value = combine_ranks(ms, N, args.steps, device=dev)
 
@@ -411,6 +476,20 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.e2e_steps
     _, e2e_value = combine_ranks(e2e_ms, N, 1, device=dev)
+    # the copies of one e2e step alone (same pinned buffers, same stream): H2D of x and gamma,
+    # D2H of u and S
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c2 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    X.copy_(xh, non_blocking=True)
+    G.copy_(gh, non_blocking=True)
+    c1.record(stream)
+    uh.copy_(U, non_blocking=True)
+    sh.copy_(S, non_blocking=True)
+    c2.record(stream)
+    torch.cuda.synchronize()
+    copy_ms = (c0.elapsed_time(c1), c1.elapsed_time(c2))
     if rank != 0:
         if ws > 1:
             torch.distributed.barrier()
@@ -433,10 +512,17 @@ def main():
     phases_alone = {k: round(statistics.mean(p[k] for p in alone), 3) for k in alone[0]}
     R, Rc = info["near_rings"], info["correction_rings"]
     pairs, flops = p2p_work(f["x"], 2 * math.pi, info["depth"], R, sigma, Rc, args.rho_cut)
-    achieved = flops / (p2p_ms / 1e3) / 1e12
+    achieved_kernel = flops / (p2p_ms / 1e3) / 1e12
+    achieved = ALGO_FLOPS_PER_PAIR * pairs / (p2p_ms / 1e3) / 1e12
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    peak = 2 * 128 * sms * 2.070e9 / 1e12
+    measured = measure_peaks(dev, stream) if args.peaks else None
+    if measured:
+        peak = measured["fp32_ffma"]
+        peak_basis = "measured: FFMA probe (vfmm_probe_peak), burst"
+    else:
+        peak = 2 * 128 * sms * 2.070e9 / 1e12
+        peak_basis = "derived: 2 x 128 FP32 lanes x %d SMs x 2070 MHz" % sms
     traffic = profiled_traffic("k_p2p_f32", ["p2p.cu"], N)
     phases = {k: round(statistics.mean(p[k] for p in phase_ms), 3) for k in phase_ms[0]}
 
@@ -454,15 +540,38 @@ def main():
     except Exception:
         pass
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    if args.m2l == "tf32x3" and measured:
+        m2l_peak, m2l_basis = measured["tf32_tcgen05"], "measured TF32 tcgen05 probe, burst"
+    elif args.m2l == "tf32x3":
+        m2l_peak, m2l_basis = bf16_peak / 2, "measured BF16 burst x 1/2 (nominal TF32:BF16 ratio)"
+    else:
+        m2l_peak = bf16_peak
+        m2l_basis = "measured BF16 burst (cuBLAS)" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s"
     m2l_achieved = m2l_flops / (phases_alone["m2l"] / 1e3) / 1e12
-    roof_m2l = {"bound": "tensor", "achieved": m2l_achieved, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": m2l_achieved / bf16_peak, "kernel": "k_m2l_lines / k_m2l_tc (levels 3..D)",
-                "flops_per_eval": m2l_flops,
-                "peak_basis": "measured BF16 burst" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s",
+    roof_m2l = {"bound": "tensor", "achieved": m2l_achieved, "peak": m2l_peak, "unit": "TFLOP/s",
+                "frac": m2l_achieved / m2l_peak, "kernel": "k_m2l_lines / k_m2l_tc (levels 3..D)",
+                "flops_per_eval": m2l_flops, "peak_basis": m2l_basis,
                 "m2l_prec": args.m2l}
 
     out_err = {}
-    if args.check:
+    if timed_out is not None:
+        # the timed handle (27^3 images) against the oracle's full 27^3-box sum at the stored
+        # targets: central 27 boxes + far-image increment (tests/golden/make_field256.py)
+        full = ~np.isnan(gold["u_far"][:, 0])
+        uo = gold["u_near"][full] + gold["u_far"][full]
+        so = gold["S_near"][full] + gold["S_far"][full]
+        ut, st = timed_out[0][full], timed_out[1][full]
+        pu = np.linalg.norm(ut - uo, axis=1) / np.linalg.norm(uo, axis=1)
+        ps = np.linalg.norm(st - so, axis=1) / np.linalg.norm(so, axis=1)
+        face = gold["face"][full]
+        out_err = {"rel_l2_u": float(np.linalg.norm(ut - uo) / np.linalg.norm(uo)),
+                   "rel_l2_S": float(np.linalg.norm(st - so) / np.linalg.norm(so)),
+                   "max_rel_target_u": float(pu.max()), "max_rel_target_S": float(ps.max()),
+                   "targets": int(full.sum()), "face_targets": int(face.sum()),
+                   "images": "27^3 boxes (the timed handle, S=2)",
+                   "oracle": "FP64 direct sum, central 27 boxes + far-image increment, stored in "
+                             "tests/golden/field256_k4_seed1.txt"}
+    elif args.check:
         import oracle
         tid = wl.target_subset(N, args.check, seed=3)
         uo, so = oracle.direct(f["x"], f["alpha"], sigma, K=1, targets=tid)
@@ -473,8 +582,11 @@ def main():
         u0 = u0.double().cpu().numpy()[tid]
         s0 = s0.double().cpu().numpy()[tid]
         h0.close()
+        pu = np.linalg.norm(u0 - uo, axis=1) / np.linalg.norm(uo, axis=1)
+        ps = np.linalg.norm(s0 - so, axis=1) / np.linalg.norm(so, axis=1)
         out_err = {"rel_l2_u": float(np.linalg.norm(u0 - uo) / np.linalg.norm(uo)),
                    "rel_l2_S": float(np.linalg.norm(s0 - so) / np.linalg.norm(so)),
+                   "max_rel_target_u": float(pu.max()), "max_rel_target_S": float(ps.max()),
                    "targets": args.check, "images": "27 central boxes (same tree, S=0)"}
 
     cb = cpu_baseline(f, args.cpu_targets or os.cpu_count()) if ws == 1 else None
@@ -491,14 +603,19 @@ def main():
                    "correction_rings": Rc, "rho_cut": args.rho_cut,
                    "l2": "inputs (x, gamma %d MiB) larger than L2 (129 MB); no flush" % (2 * N * 3 * 4 // 2 ** 20),
                    "parallelism": "replicas" if ws > 1 else "single"},
-        "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms, "h2d_ms_alone": copy_ms[0], "d2h_ms_alone": copy_ms[1],
+                "h2d_gbs": h2d / (copy_ms[0] / 1e3) / 1e9, "d2h_gbs": d2h / (copy_ms[1] / 1e3) / 1e9},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_p2p_f32",
-                     "pairs_per_launch": pairs, "flops_per_launch": flops,
-                     "flops_per_pair": {"smoothed": FLOPS_PER_PAIR, "singular": FLOPS_PER_PAIR_SINGULAR},
-                     "peak_basis": "2 x 128 FP32 lanes x %d SMs x 2070 MHz" % sms},
+                     "pairs_per_launch": pairs, "algorithmic_flops_per_pair": ALGO_FLOPS_PER_PAIR,
+                     "kernel_flops_per_launch": flops, "achieved_kernel_flops": achieved_kernel,
+                     "frac_kernel_flops": achieved_kernel / peak,
+                     "kernel_flops_per_pair": {"smoothed": FLOPS_PER_PAIR, "singular": FLOPS_PER_PAIR_SINGULAR},
+                     "peak_basis": peak_basis},
         "roofline_m2l": roof_m2l,
+        "peaks": measured,
         "excluding_tree_build": {"value": N / (eval_ms / 1e3), "unit": "particles/s", "ms_per_eval": eval_ms,
                                  "note": "median over the timed steps of vfmm_eval_velocity_stretching alone"},
         "phases_ms": phases,

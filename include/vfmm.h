@@ -112,11 +112,21 @@ int vfmm_destroy(vfmm_handle h);
 /* Change the stream later calls enqueue on. */
 int vfmm_set_stream(vfmm_handle h, void *stream);
 
+/* Tries of each bounded wait in the tensor-core M2L pipeline before a CTA gives up (0 = the
+ * default, 2^26).  A CTA that gives up stops its pipeline, waits for its own copies and MMAs to
+ * complete, frees its tensor memory and sets the timeout bit: the evaluation then reports
+ * VFMM_ERR_TIMEOUT at vfmm_sync and its outputs are not valid; the handle stays usable.  A
+ * small limit makes the waits give up on purpose, which is how that path is tested (failure
+ * injection; the paper has no counterpart).  Errors: tries < 0 -> VFMM_ERR_ARG. */
+int vfmm_set_wait_limit(vfmm_handle h, int64_t tries);
+
 /* Sort n particles into the uniform octree (Section 3.2; tree construction ran on the CPU in
  * the paper, Section 2.2).  x: device n x 3 positions; positions are wrapped into [0, L)^3
  * by x - L floor(x/L) (any finite value is accepted).  Keys are leaf indices, the sort is a
  * counting sort with a per-leaf index sort, so the order is deterministic.
- * Errors: n <= 0 -> VFMM_ERR_ARG; a leaf with more than 4096 particles -> VFMM_ERR_UNSUPPORTED. */
+ * Errors: n <= 0 -> VFMM_ERR_ARG; a NaN or infinite coordinate -> VFMM_ERR_ARG (detected on the
+ * device, reported by this call, which synchronises; the handle then has no tree); a leaf with
+ * more than 4096 particles -> VFMM_ERR_UNSUPPORTED. */
 int vfmm_build_tree(vfmm_handle h, int64_t n, const void *x);
 
 /* u and S at every particle for strengths gamma (device n x 3, caller order) and core
@@ -135,14 +145,22 @@ int vfmm_eval_velocity_stretching(vfmm_handle h, const void *gamma, double sigma
 int vfmm_eval_velocity_gradient(vfmm_handle h, const void *gamma, double sigma, void *u_out, void *g_out);
 
 /* Adjoint of u = A(x) gamma for a loss L(u) with w = dL/du (device n x 3, caller order), on the
- * tree of the last vfmm_build_tree (positions frozen):
- *   dgamma = A^T w = A w   (the Biot-Savart matrix is symmetric: A_ji = A_ij^T),
- *   dx_m   = (grad u^gamma(x_m))^T w_m + (grad u^w(x_m))^T gamma_m,
- * where u^w is the velocity induced by strengths w.  With VFMM_METHOD_DIRECT this is the exact
- * gradient of the evaluated sum; with the FMM, dgamma applies the FMM operator to w, which
- * equals the transpose of the FMM operator to the FMM's accuracy.  v (dL/dS) must be NULL
- * (VFMM_ERR_UNSUPPORTED otherwise).  dgamma, dx: device n x 3.  Uses handle-owned temporaries
- * of 21 n values. */
+ * tree of the last vfmm_build_tree (positions frozen to their leaves):
+ *   dgamma = A^T w,   dx_m = dL/dx_m,
+ * the exact gradient (to rounding) of u as vfmm_eval_velocity_gradient evaluates it.  With
+ * VFMM_METHOD_DIRECT, A^T w = A w (the Biot-Savart matrix is symmetric: A_ji = A_ij^T) and
+ * dx_m = (grad u^gamma(x_m))^T w_m + (grad u^w(x_m))^T gamma_m, u^w the velocity of strengths w.
+ * With the FMM, A^T is the transpose of the evaluated operator: the near field (all near rings
+ * with the smoothed kernel, a symmetric pair set) as for the direct sum, and the far field run
+ * backwards through the transposed chain (transposed L2P as a P2M of the curl of the local basis,
+ * L2L^T, M2L^T with the transposed translation matrices, lattice and root M2M transposed in
+ * FP64, M2M^T, P2M^T as an evaluation of the dual multipole); dx_m adds to the target term the
+ * source term gamma_m . grad of that dual potential.  The transposed operators are built on the
+ * first FMM call (host FP64, then uploaded: 2 x 343 matrices of 128 x 128 and their tensor-core
+ * tiles).  In FP32 the velocity-gradient path (all near rings smoothed) is the operator; it agrees
+ * with vfmm_eval_velocity_stretching's one ring + Gaussian-tail correction to the FMM tolerance.
+ * v (dL/dS) must be NULL (VFMM_ERR_UNSUPPORTED otherwise).  dgamma, dx: device n x 3.  Uses
+ * handle-owned temporaries of 21 n values. */
 int vfmm_eval_adjoint(vfmm_handle h, const void *gamma, double sigma, const void *w, const void *v, void *dgamma,
                       void *dx);
 
@@ -215,6 +233,29 @@ int vfmm_get_timings(vfmm_handle h, double *ms_per_phase, int nphase);
  * Writes min(nout, 7) values. */
 int vfmm_get_tree_info(vfmm_handle h, int64_t *out, int nout);
 
+/* Peak-rate probes, the measured denominators of the roofline fractions (measurement only;
+ * the paper has no counterpart).  Launches one kernel on stream (a cudaStream_t) on the
+ * current device that performs *ops operations of one kind, for the caller to time with CUDA
+ * events on that stream:
+ *   VFMM_PROBE_FFMA   FP32 fmaf, 8 independent chains per thread, 64 warps per SM; 2 flops each
+ *   VFMM_PROBE_EX2    MUFU ex2.approx.ftz.f32; 1 op per lane
+ *   VFMM_PROBE_RSQRT  MUFU rsqrt.approx.ftz.f32; 1 op per lane
+ *   VFMM_PROBE_DFMA   FP64 fma; 2 flops each
+ *   VFMM_PROBE_MMA_TF32 / _BF16  one CTA per SM issuing tcgen05.mma (M 128, N 256, K 8 TF32 /
+ *                     16 BF16, shared-memory operands, TMEM accumulator); 2 M N K flops each
+ * reps scales the work (the ALU probes run 128 reps of each chain step per unit; the MMA
+ * probes reps instructions per SM).  err_dev: device int that the MMA probes OR with 4
+ * (timeout of their bounded completion wait); may be NULL for the ALU probes.  Nothing is
+ * allocated.  Errors: unknown kind, reps <= 0, ops NULL, or err_dev NULL for an MMA probe ->
+ * VFMM_ERR_ARG; a failed launch -> VFMM_ERR_CUDA. */
+#define VFMM_PROBE_FFMA 0
+#define VFMM_PROBE_EX2 1
+#define VFMM_PROBE_RSQRT 2
+#define VFMM_PROBE_DFMA 3
+#define VFMM_PROBE_MMA_TF32 4
+#define VFMM_PROBE_MMA_BF16 5
+int vfmm_probe_peak(int kind, int64_t reps, void *stream, int *err_dev, double *ops);
+
 /* Largest n accepted by vfmm_direct_eval_noalloc. */
 #define VFMM_NOALLOC_MAX_N 65536
 
@@ -233,8 +274,11 @@ int vfmm_get_tree_info(vfmm_handle h, int64_t *out, int nout);
  * every device that loads the library until the process exits.  Every call on a device uses
  * the same array and overwrites the part it needs, so calls whose work overlaps on the GPU
  * (other streams, other host threads) race: order them on one stream or synchronise between.
- * The first call on a device, with that device current, looks up the array's device address
- * (cudaGetSymbolAddress) once; make that first call before any stream capture.
+ * Each call outside stream capture looks up the array's device address (cudaGetSymbolAddress,
+ * with the device current; a host-side lookup that allocates nothing), so the address stays
+ * right after cudaDeviceReset reloads the module; a call during stream capture reuses the
+ * address of the last call outside capture on that device, so make a first call before any
+ * capture (a capture with no earlier call does the lookup itself).
  * Errors: n <= 0, a NULL x/gamma/u_out, sigma or box not finite and > 0, or images outside
  * [0, 20] -> VFMM_ERR_ARG; n > VFMM_NOALLOC_MAX_N -> VFMM_ERR_UNSUPPORTED (nothing is
  * launched); a failed address look-up or launch -> VFMM_ERR_CUDA. */

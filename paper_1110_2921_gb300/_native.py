@@ -26,6 +26,12 @@ VFMM_M2L_TF32X3 = 2
 VFMM_M2L_BF16X3 = 3
 VFMM_METHOD_FMM = 0
 VFMM_METHOD_DIRECT = 1
+VFMM_PROBE_FFMA = 0
+VFMM_PROBE_EX2 = 1
+VFMM_PROBE_RSQRT = 2
+VFMM_PROBE_DFMA = 3
+VFMM_PROBE_MMA_TF32 = 4
+VFMM_PROBE_MMA_BF16 = 5
 
 
 class vfmm_config(ctypes.Structure):
@@ -60,6 +66,7 @@ def lib():
             "vfmm_create": ([ctypes.POINTER(vfmm_config), ctypes.POINTER(H)], ctypes.c_int),
             "vfmm_destroy": ([H], ctypes.c_int),
             "vfmm_set_stream": ([H, V], ctypes.c_int),
+            "vfmm_set_wait_limit": ([H, ctypes.c_int64], ctypes.c_int),
             "vfmm_build_tree": ([H, ctypes.c_int64, V], ctypes.c_int),
             "vfmm_eval_velocity_stretching": ([H, V, ctypes.c_double, V, V], ctypes.c_int),
             "vfmm_eval_host": ([H, ctypes.c_int64, V, V, ctypes.c_double, V, V], ctypes.c_int),
@@ -75,6 +82,7 @@ def lib():
             "vfmm_sync": ([H], ctypes.c_int),
             "vfmm_get_timings": ([H, ctypes.POINTER(ctypes.c_double), ctypes.c_int], ctypes.c_int),
             "vfmm_get_tree_info": ([H, ctypes.POINTER(ctypes.c_int64), ctypes.c_int], ctypes.c_int),
+            "vfmm_probe_peak": ([ctypes.c_int, ctypes.c_int64, V, V, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             "vfmm_strerror": ([ctypes.c_int], ctypes.c_char_p),
             "vfmm_last_error": ([H], ctypes.c_char_p),
         }
@@ -116,6 +124,10 @@ def vfmm_destroy(h):
 
 def vfmm_set_stream(h, stream_ptr):
     check(lib().vfmm_set_stream(h, ctypes.c_void_p(stream_ptr)), "vfmm_set_stream", h)
+
+
+def vfmm_set_wait_limit(h, tries):
+    check(lib().vfmm_set_wait_limit(h, int(tries)), "vfmm_set_wait_limit", h)
 
 
 def vfmm_build_tree(h, n, x_ptr):
@@ -195,3 +207,12 @@ def vfmm_get_tree_info(h):
     check(lib().vfmm_get_tree_info(h, buf, 7), "vfmm_get_tree_info", h)
     return {"depth": buf[0], "near_rings": buf[1], "leaves_per_side": buf[2],
             "max_leaf": buf[3], "n": buf[4], "launches": buf[5], "correction_rings": buf[6]}
+
+
+def vfmm_probe_peak(kind, reps, stream_ptr, err_ptr=None):
+    """Launch one peak-rate probe on the stream; returns the operations it performs."""
+    ops = ctypes.c_double(0.0)
+    check(lib().vfmm_probe_peak(int(kind), int(reps), ctypes.c_void_p(stream_ptr),
+                                ctypes.c_void_p(err_ptr) if err_ptr else None, ctypes.byref(ops)),
+          "vfmm_probe_peak")
+    return ops.value

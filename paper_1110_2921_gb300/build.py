@@ -13,8 +13,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvfmm.so")
+# the checked build (-DVFMM_CHECK=1: gather indices range-checked) lives beside it
+CHECK_DIR = os.path.join(HERE, "_build_check")
+CHECK_LIB = os.path.join(CHECK_DIR, "libvfmm.so")
 SOURCES = ["api.cu", "operators.cpp", "tree.cu", "p2p.cu", "expansions.cu", "m2l_tc.cu", "integrate.cu", "reinit.cu",
-           "diagnostics.cu"]
+           "diagnostics.cu", "probes.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 
@@ -37,22 +40,26 @@ def _deps():
     return files
 
 
-def needs_build():
-    if not os.path.exists(LIB):
+def needs_build(lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force=False, verbose=False, extra=()):
-    """Compile and link; returns the library path."""
-    if not force and not needs_build():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force=False, verbose=False, extra=(), checked=False):
+    """Compile and link; returns the library path.  checked=True builds the range-checked
+    variant (-DVFMM_CHECK=1) into _build_check/ instead."""
+    out_dir, lib = (CHECK_DIR, CHECK_LIB) if checked else (OUT_DIR, LIB)
+    if checked:
+        extra = tuple(extra) + ("-DVFMM_CHECK=1",)
+    if not force and not needs_build(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(out_dir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc, *_flags(), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc, *_flags(), *extra, "-x", "c++", "-c", os.path.join(CSRC, src), "-o", obj]
@@ -65,13 +72,13 @@ def build(force=False, verbose=False, extra=()):
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc, "-shared", "-gencode", GENCODE, "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <utility>
 
 struct vfmm_ctx {
     vfmm::Ctx c;
@@ -221,6 +222,149 @@ template <typename T> int build_operators(Ctx *c)
     return VFMM_OK;
 }
 
+// Transposed operators of the adjoint: at index t of the M2L set the transpose of the forward
+// operator of offset -t (the interaction lists are symmetric, so the same lists apply), L2L_b^T
+// and M2M_b^T for the child octants, and the tensor-core tiles of the transposed M2L set.
+std::vector<double> transpose_sq(const std::vector<double> &A, int nc)
+{
+    std::vector<double> B(A.size());
+    for (int i = 0; i < nc; ++i)
+        for (int j = 0; j < nc; ++j) B[(size_t)j * nc + i] = A[(size_t)i * nc + j];
+    return B;
+}
+
+template <typename T> int build_transposed(Ctx *c)
+{
+    const int p = c->p, nc = c->nc, pc = c->pc;
+    const bool tc = c->cfg.m2l_prec == VFMM_M2L_TF32X3 || c->cfg.m2l_prec == VFMM_M2L_BF16X3;
+    const bool bf16 = c->cfg.m2l_prec == VFMM_M2L_BF16X3;
+    const size_t tile_bytes = (size_t)pc * (bf16 ? 2 : 4) / TC_KBYTES * TC_A_TILE;
+    std::vector<T> m2l((size_t)NT * pc * OUT_ROWS, T(0));
+    std::vector<unsigned char> thi, tlo;
+    if (tc) {
+        thi.assign((size_t)NT * tile_bytes, 0);
+        tlo.assign((size_t)NT * tile_bytes, 0);
+    }
+    for (int tx = -3; tx <= 3; ++tx)
+        for (int ty = -3; ty <= 3; ++ty)
+            for (int tz = -3; tz <= 3; ++tz) {
+                if (std::abs(tx) <= 1 && std::abs(ty) <= 1 && std::abs(tz) <= 1) continue;
+                // the forward operator of offset -t translates by d = t
+                double d[3] = {(double)tx, (double)ty, (double)tz};
+                std::vector<double> A = transpose_sq(ops::m2l_hat(d, p), nc);
+                std::vector<T> at = to_at<T>(A, nc, pc);
+                const int ti = tindex(tx, ty, tz);
+                std::copy(at.begin(), at.end(), m2l.begin() + (size_t)ti * pc * OUT_ROWS);
+                if (tc) tile_matrix(A, nc, pc, bf16, thi.data() + ti * tile_bytes, tlo.data() + ti * tile_bytes);
+            }
+    std::vector<T> m2m((size_t)8 * pc * OUT_ROWS), l2l((size_t)8 * pc * OUT_ROWS);
+    for (int b = 0; b < 8; ++b) {
+        int bx = (b >> 2) & 1, by = (b >> 1) & 1, bz = b & 1;
+        double e1[3] = {(bx - 0.5) / 2.0, (by - 0.5) / 2.0, (bz - 0.5) / 2.0};
+        std::vector<T> a1 = to_at<T>(transpose_sq(ops::m2m_hat(e1, 2.0, p), nc), nc, pc);
+        std::copy(a1.begin(), a1.end(), m2m.begin() + (size_t)b * pc * OUT_ROWS);
+        double e2[3] = {bx - 0.5, by - 0.5, bz - 0.5};
+        std::vector<T> a2 = to_at<T>(transpose_sq(ops::l2l_hat(e2, p), nc), nc, pc);
+        std::copy(a2.begin(), a2.end(), l2l.begin() + (size_t)b * pc * OUT_ROWS);
+    }
+    int st;
+    if ((st = upload_vec(c, c->at_m2l_t, m2l, "transposed M2L operators"))) return st;
+    if ((st = upload_vec(c, c->at_m2m_t, m2m, "transposed M2M operators"))) return st;
+    if ((st = upload_vec(c, c->at_l2l_t, l2l, "transposed L2L operators"))) return st;
+    if (tc) {
+        if ((st = upload_vec(c, c->tc_hi_t, thi, "transposed tensor-core M2L tiles"))) return st;
+        if ((st = upload_vec(c, c->tc_lo_t, tlo, "transposed tensor-core M2L tiles"))) return st;
+    }
+    c->have_transposed = true;
+    return VFMM_OK;
+}
+
+// The transposed far field of the strengths in c->gs (sorted): lambda_D = E^T w, then for each
+// level from the leaves up mu_l = M2L^T lambda_l and lambda_(l-1) = L2L^T lambda_l, the root
+// (mu_1 += M2M_root^T lattice^T lambda_0 when there are periodic super-levels), and from the
+// root down mu_(l+1) += M2M^T mu_l.  lambda lives in the local buffer, mu in the multipole
+// buffer; the leaf mu is left for launch_dual_l2p.  R: near rings of the leaf level.
+int far_transpose(Ctx *c, int R)
+{
+    const int D = c->depth, S = c->cfg.periodic_levels;
+    const int4 *kbd = (const int4 *)c->kblocks.p;
+    auto lvl = [&](DevBuf &b, int l) { return (void *)((char *)b.p + c->lvl_off[l] * c->esz); };
+    int rc;
+    if ((rc = launch_dual_p2m(c, c->gs.p))) return rc;
+    const bool tc = c->cfg.m2l_prec == VFMM_M2L_TF32X3 || c->cfg.m2l_prec == VFMM_M2L_BF16X3;
+    const bool bf = c->cfg.m2l_prec == VFMM_M2L_BF16X3;
+    for (int l = D; l >= 1; --l) {
+        const int Rl = (l == D) ? R : 1;
+        if (tc && l >= 3) {
+            // the tensor-core M2L reads the multipole buffer and writes the local buffer: swap the
+            // roles of the buffers and the tile sets for the transposed translation
+            std::swap(c->mexp, c->lexp);
+            std::swap(c->tc_hi, c->tc_hi_t);
+            std::swap(c->tc_lo, c->tc_lo_t);
+            rc = launch_split(c, l, bf);
+            if (!rc) rc = launch_tc_m2l(c, l, Rl, bf);
+            std::swap(c->mexp, c->lexp);
+            std::swap(c->tc_hi, c->tc_hi_t);
+            std::swap(c->tc_lo, c->tc_lo_t);
+            if (rc) return rc;
+        } else {
+            GemmParams gp = {};
+            gp.AT = c->at_m2l_t.p;
+            gp.B = lvl(c->lexp, l);
+            gp.C = lvl(c->mexp, l);
+            gp.kb = kbd;
+            for (int g = 0; g < 8; ++g) {
+                gp.kb_off[g] = c->kb_m2l_off[Rl][g];
+                gp.kb_cnt[g] = c->kb_m2l_cnt[Rl][g];
+            }
+            gp.n_src = gp.n_tgt = 1 << l;
+            gp.mode = 0;
+            gp.grouped = 1;
+            gp.accumulate = 0;
+            gp.pc = c->pc;
+            if ((rc = launch_gemm(c, gp, 8, (int64_t)1 << (3 * (l - 1))))) return rc;
+        }
+        if (l >= 2 || S > 0) {
+            // lambda_(l-1)[P] = sum_b L2L_b^T lambda_l[2P + b]
+            GemmParams gp = {};
+            gp.AT = c->at_l2l_t.p;
+            gp.B = lvl(c->lexp, l);
+            gp.C = lvl(c->lexp, l - 1);
+            gp.kb = kbd;
+            gp.kb_off[0] = c->kb_m2m_off;
+            gp.kb_cnt[0] = 8;
+            gp.n_src = 1 << l;
+            gp.n_tgt = 1 << (l - 1);
+            gp.mode = 1;
+            gp.grouped = 0;
+            gp.accumulate = 0;
+            gp.pc = c->pc;
+            if ((rc = launch_gemm(c, gp, 1, (int64_t)1 << (3 * (l - 1))))) return rc;
+        }
+    }
+    if (S > 0 && (rc = launch_root_t(c))) return rc;
+    for (int l = 1; l < D; ++l) {
+        // mu_(l+1)[c] += M2M_(parity c)^T mu_l[c >> 1]
+        GemmParams gp = {};
+        gp.AT = c->at_m2m_t.p;
+        gp.B = lvl(c->mexp, l);
+        gp.C = lvl(c->mexp, l + 1);
+        gp.kb = kbd;
+        for (int g = 0; g < 8; ++g) {
+            gp.kb_off[g] = c->kb_l2l_off[g];
+            gp.kb_cnt[g] = 1;
+        }
+        gp.n_src = 1 << l;
+        gp.n_tgt = 1 << (l + 1);
+        gp.mode = 2;
+        gp.grouped = 1;
+        gp.accumulate = 1;
+        gp.pc = c->pc;
+        if ((rc = launch_gemm(c, gp, 8, (int64_t)1 << (3 * l)))) return rc;
+    }
+    return VFMM_OK;
+}
+
 int check_device_error(Ctx *c)
 {
     int e = 0;
@@ -232,12 +376,16 @@ int check_device_error(Ctx *c)
         if (e & ERRBIT_LEAF_OVERFLOW)
             return fail(c, VFMM_ERR_UNSUPPORTED, "a leaf holds more particles than the per-leaf sort capacity (4096); use a deeper tree");
         if (e & ERRBIT_TIMEOUT) return fail(c, VFMM_ERR_TIMEOUT, "a bounded device wait gave up");
+        if (e & ERRBIT_NONFINITE) return fail(c, VFMM_ERR_ARG, "a position is NaN or infinite");
         return fail(c, VFMM_ERR_BOUNDS, "a device bounds check fired");
     }
     return VFMM_OK;
 }
 
-int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out, bool grad = false)
+// near_only (with grad): the near-field P2P alone, no far field (the adjoint adds the
+// transposed far field itself)
+int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out, bool grad = false,
+              bool near_only = false)
 {
     if (!c->built) return fail(c, VFMM_ERR_NOT_BUILT, "vfmm_build_tree has not been called");
     if (!gamma || !u_out) return fail(c, VFMM_ERR_ARG, "null gamma or u_out");
@@ -282,7 +430,7 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
         cudaStream_t s;
         ~Restore() { c->stream = s; }
     } restore{c, main_st};
-    if (fmm) {
+    if (fmm && !near_only) {
         const int D = c->depth;
         const int S = c->cfg.periodic_levels;
         const int4 *kbd = (const int4 *)c->kblocks.p;
@@ -558,7 +706,7 @@ int vfmm_destroy(vfmm_handle h)
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->xs, &c->gs, &c->perm, &c->keys, &c->leaf_start, &c->counts, &c->fill, &c->tmpidx,
                       &c->scan_part, &c->err, &c->maxleaf, &c->bbox, &c->oct_start, &c->oct_box, &c->mexp, &c->lexp, &c->mhi, &c->mlo, &c->gemm_part, &c->ufar,
-                      &c->sfar, &c->gfar, &c->adj_u, &c->adj_g1, &c->adj_g2, &c->rk_u1, &c->rk_s1, &c->rk_u2, &c->rk_s2, &c->rk_x1, &c->rk_g1, &c->diag, &c->rg_om, &c->rg_r, &c->rg_d, &c->rg_q, &c->rg_t1, &c->rg_t2, &c->rg_dots, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->m2m_f64,
+                      &c->sfar, &c->gfar, &c->adj_u, &c->adj_g1, &c->adj_g2, &c->rk_u1, &c->rk_s1, &c->rk_u2, &c->rk_s2, &c->rk_x1, &c->rk_g1, &c->diag, &c->rg_om, &c->rg_r, &c->rg_d, &c->rg_q, &c->rg_t1, &c->rg_t2, &c->rg_dots, &c->at_m2l, &c->at_m2m, &c->at_l2l, &c->tc_hi, &c->tc_lo, &c->at_m2l_t, &c->at_m2m_t, &c->at_l2l_t, &c->tc_hi_t, &c->tc_lo_t, &c->m2m_f64,
                       &c->lattice_f64, &c->root_m, &c->kblocks, &c->cls, &c->spec_work, &c->spec_E, &c->hx, &c->hg, &c->hu, &c->hs};
     for (DevBuf *b : bufs) release(*b);
     if (c->have_events)
@@ -573,6 +721,15 @@ int vfmm_set_stream(vfmm_handle h, void *stream)
     if (!h) return VFMM_ERR_ARG;
     h->c.stream = (cudaStream_t)stream;
     h->c.cfg.stream = stream;
+    return VFMM_OK;
+}
+
+int vfmm_set_wait_limit(vfmm_handle h, int64_t tries)
+{
+    if (!h) return VFMM_ERR_ARG;
+    Ctx *c = &h->c;
+    if (tries < 0) return fail(c, VFMM_ERR_ARG, "tries must be >= 0");
+    c->wait_limit = tries > 0 ? (long long)tries : (1LL << 26);
     return VFMM_OK;
 }
 
@@ -613,10 +770,27 @@ int vfmm_eval_adjoint(vfmm_handle h, const void *gamma, double sigma, const void
     if ((st = ensure(c, c->adj_u, n * 3 * c->esz, "adjoint velocity"))) return st;
     if ((st = ensure(c, c->adj_g1, n * 9 * c->esz, "adjoint gradient"))) return st;
     if ((st = ensure(c, c->adj_g2, n * 9 * c->esz, "adjoint gradient"))) return st;
-    // grad u of the gamma field, then velocity and grad u of the w field (dL/dgamma = A w)
+    if (c->cfg.method != VFMM_METHOD_FMM) {
+        // direct sum: grad u of the gamma field, then velocity and grad u of the w field
+        // (dL/dgamma = A w, A symmetric)
+        if ((st = vfmm_eval_velocity_gradient(h, gamma, sigma, c->adj_u.p, c->adj_g1.p))) return st;
+        if ((st = vfmm_eval_velocity_gradient(h, w, sigma, dgamma, c->adj_g2.p))) return st;
+        return launch_adjoint_combine(c, c->adj_g1.p, w, c->adj_g2.p, gamma, nullptr, dx);
+    }
+    // FMM: the exact transpose of the evaluated operator.  (1) grad u of the gamma field (near
+    // and far: the target-position term); (2) the near field of w (symmetric pair set: its
+    // velocity is the near part of A^T w, its gradient gives the near source-position term);
+    // (3) the transposed far field of w adds P^T ... E^T w to dgamma and writes the far
+    // source-position term; (4) dx = G1^T w + G2_near^T gamma + far term.
+    if (!c->have_transposed) {
+        st = c->f64 ? build_transposed<double>(c) : build_transposed<float>(c);
+        if (st) return st;
+    }
     if ((st = vfmm_eval_velocity_gradient(h, gamma, sigma, c->adj_u.p, c->adj_g1.p))) return st;
-    if ((st = vfmm_eval_velocity_gradient(h, w, sigma, dgamma, c->adj_g2.p))) return st;
-    return launch_adjoint_combine(c, c->adj_g1.p, w, c->adj_g2.p, gamma, dx);
+    if ((st = eval_impl(c, w, sigma, dgamma, c->adj_g2.p, true, true))) return st;
+    if ((st = far_transpose(c, c->last_R))) return st;
+    if ((st = launch_dual_l2p(c, gamma, dgamma, c->adj_u.p))) return st;
+    return launch_adjoint_combine(c, c->adj_g1.p, w, c->adj_g2.p, gamma, c->adj_u.p, dx);
 }
 
 int vfmm_rk_step(vfmm_handle h, int64_t n, void *x, void *gamma, double *sigma, double dt, double nu)

@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(GTHREADS) k_gemm(GemmParams gp, int64_t ncell_
         for (int s = 0; s < 2; ++s) {
             if (slot_ok[s]) {
                 int64_t src = source_cell(gp, slot_cx[s], slot_cy[s], slot_cz[s], kb);
+                src = checked_index<int64_t>(src, (int64_t)gp.n_src * gp.n_src * gp.n_src, gp.err);
                 rb[s] = *(const vec *)(B + (src * 3 + slot_comp[s]) * pc + j0 + slot_part[s] * VEC);
             } else {
                 T *z = (T *)&rb[s];
@@ -466,6 +467,7 @@ int launch_gemm(Ctx *c, const GemmParams &gp_in, int ngroups, int64_t ncell_grou
     }
     gp.ksplit = ksplit;
     gp.partial = c->gemm_part.p;
+    gp.err = (int *)c->err.p;
     grid.z = (unsigned)ksplit;
     if (c->f64)
         k_gemm<double><<<grid, GTHREADS, 0, c->stream>>>(gp, ncell_group);
@@ -845,6 +847,300 @@ int launch_add_far(Ctx *c, void *u_out, void *s_out)
     const int nb = (int)((c->n + 255) / 256);
     k_add_far<<<nb, 256, 0, c->stream>>>(c->n, (const int *)c->perm.p, (const float *)c->ufar.p, (const float *)c->sfar.p,
                                          (float *)u_out, (float *)s_out);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+}  // namespace vfmm
+
+namespace vfmm {
+
+// ---------------------------------------------------------------------------------------
+// Transposed far field (the adjoint of the FMM evaluation, Section 3.1 run backwards).
+//
+// The far velocity is u_far = E Lc(L2L) (M2L + lattice) Mc(M2M) P gamma: P the P2M, the
+// expansion chains, and E the L2P curl of the leaf local expansion,
+//   u_a(x_i) = 1/(4 pi w^2) sum_{b,c,k} eps_abc L[c][k] d_b phi_k(x^_i),
+//   phi_(n,m,re|im) = wgt_m s_nm Re|Im Y_n^m (wgt_0 = 1, wgt_m = 2), x^ = (x - z)/w.
+// Its exact transpose applied to w = dL/du runs the chain backwards:
+//   E^T:  lambda[c][k] = 1/(4 pi w^2) wgt_m s_nm sum_i (w_i x grad^ Re|Im Y_n^m(x^_i))_c,
+//   L2L^T, M2L^T, lattice^T, M2M^T: the same GEMMs with transposed matrices (host-built),
+//   P^T:  mu -> Phi_c(x_j) = sum_k mu[c][k] s_nm Re|Im Y_n^m(x^_j)  (dL/dgamma_j, far part),
+// and the source-position term of dL/dx_j is sum_c gamma_jc grad Phi_c(x_j).
+// Gradients of Y_n^m use d/dz Y_n^m = Y_{n-1}^m, d/dx Y_n^m = (Y_{n-1}^{m+1} - Y_{n-1}^{m-1})/2,
+// d/dy Y_n^m = -i (Y_{n-1}^{m+1} + Y_{n-1}^{m-1})/2, Y_n^{-m} = (-1)^m conj Y_n^m.
+
+// Y_n^m (m >= 0, unscaled) of one point for degrees 0..nmax at cix(n, m)
+template <typename T>
+__device__ __forceinline__ void y_table(T x, T y, T z, int nmax, typename C2<T>::type *Y)
+{
+    const T r2 = x * x + y * y + z * z;
+    T dre = 1, dim = 0;
+    for (int m = 0; m <= nmax; ++m) {
+        if (m > 0) {
+            T f = -inv2m_t<T>(m);
+            T nre = f * (x * dre - y * dim);
+            T nim = f * (x * dim + y * dre);
+            dre = nre;
+            dim = nim;
+        }
+        Y[cix(m, m)].x = dre;
+        Y[cix(m, m)].y = dim;
+        T pre = dre, pim = dim, ppre = 0, ppim = 0;
+        for (int n = m + 1; n <= nmax; ++n) {
+            T c1 = T(2 * n - 1) * z, f = rec_t<T>(n, m);
+            T cre = (c1 * pre - r2 * ppre) * f;
+            T cim = (c1 * pim - r2 * ppim) * f;
+            Y[cix(n, m)].x = cre;
+            Y[cix(n, m)].y = cim;
+            ppre = pre;
+            ppim = pim;
+            pre = cre;
+            pim = cim;
+        }
+    }
+}
+
+// packed coefficient index -> (n, m, part): [n^2] = Re A_n^0, [n^2 + 2m - 1] = Re, [n^2 + 2m] = Im
+__device__ __forceinline__ void unpack_k(int k, int &n, int &m, int &part)
+{
+    n = 0;
+    while ((n + 1) * (n + 1) <= k) ++n;
+    const int r = k - n * n;
+    m = (r + 1) >> 1;
+    part = (r > 0 && (r & 1) == 0) ? 1 : 0;
+}
+
+// Re (part 0) or Im (part 1) of grad^ Y_n^m, n >= 1, from a table of degrees <= nmax >= n - 1
+template <typename T>
+__device__ __forceinline__ void y_grad_part(const typename C2<T>::type *Y, int nmax, int n, int m, int part, T &gx,
+                                            T &gy, T &gz)
+{
+    typedef typename C2<T>::type T2;
+    const T2 P = getcx<T>(Y, n - 1, m + 1, nmax), Q = getcx<T>(Y, n - 1, m - 1, nmax), Z = getcx<T>(Y, n - 1, m, nmax);
+    if (part == 0) {
+        gx = T(0.5) * (P.x - Q.x);
+        gy = T(0.5) * (P.y + Q.y);
+        gz = Z.x;
+    } else {
+        gx = T(0.5) * (P.y - Q.y);
+        gy = T(-0.5) * (P.x + Q.x);
+        gz = Z.y;
+    }
+}
+
+// E^T: per leaf, lambda[c][k] from the particles' w (sorted, in ws).  One block per leaf; a chunk
+// of particles writes its Y tables (degrees < p) to shared memory, then thread k accumulates
+// coefficient k over the chunk.
+template <typename T> struct DualCfg {
+    static constexpr int TP = sizeof(T) == 4 ? 64 : 32;  // particles per chunk
+};
+constexpr int DUAL_BS = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(DUAL_BS) k_dual_p2m(const typename V4<T>::type *__restrict__ xs,
+                                                     const typename V4<T>::type *__restrict__ ws,
+                                                     const int *__restrict__ ls, int nside, int log2n, T w, int p,
+                                                     int pc, T *__restrict__ Lam)
+{
+    typedef typename C2<T>::type T2;
+    constexpr int TP = DualCfg<T>::TP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ny = p * (p + 1) / 2;  // complex entries of degrees < p
+    T2 *Ysm = (T2 *)smem_raw;                                   // [TP][ny]
+    typename V4<T>::type *wsm = (typename V4<T>::type *)(Ysm + TP * ny);  // [TP]
+    const int leaf = blockIdx.x;
+    const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
+    const T zx = (cx + T(0.5)) * w, zy = (cy + T(0.5)) * w, zz = (cz + T(0.5)) * w;
+    const T invw = T(1) / w;
+    const int b = ls[leaf], e = ls[leaf + 1];
+    const int nc = (p + 1) * (p + 1);
+    const int k = threadIdx.x;
+    int n = 0, m = 0, part = 0;
+    if (k < nc) unpack_k(k, n, m, part);
+    T a0 = 0, a1 = 0, a2 = 0;
+    for (int s0 = b; s0 < e; s0 += TP) {
+        const int cnt = min(TP, e - s0);
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            const typename V4<T>::type xp = xs[s0 + threadIdx.x];
+            wsm[threadIdx.x] = ws[s0 + threadIdx.x];
+            y_table<T>((xp.x - zx) * invw, (xp.y - zy) * invw, (xp.z - zz) * invw, p - 1, Ysm + threadIdx.x * ny);
+        }
+        __syncthreads();
+        if (k < nc && n >= 1) {
+            for (int t = 0; t < cnt; ++t) {
+                T gx, gy, gz;
+                y_grad_part<T>(Ysm + t * ny, p - 1, n, m, part, gx, gy, gz);
+                const typename V4<T>::type wv = wsm[t];
+                a0 += wv.y * gz - wv.z * gy;
+                a1 += wv.z * gx - wv.x * gz;
+                a2 += wv.x * gy - wv.y * gx;
+            }
+        }
+    }
+    if (k < pc) {
+        T sc = 0;
+        if (k < nc) sc = T(0.0795774715459476679) * invw * invw * (m > 0 ? T(2) : T(1)) * sfac_t<T>(n, m);
+        T *out = Lam + (size_t)leaf * 3 * pc;
+        out[k] = sc * a0;
+        out[pc + k] = sc * a1;
+        out[2 * pc + k] = sc * a2;
+    }
+}
+
+// P^T and the source-position term: per particle j of a leaf with dual multipole mu,
+//   dgamma[perm j][c] += Phi_c(x_j),  dxf[perm j] = sum_c gamma_jc grad Phi_c(x_j)  (caller order).
+constexpr int DUAL_L2P_BS = 64;
+template <typename T>
+__global__ void __launch_bounds__(DUAL_L2P_BS) k_dual_l2p(const typename V4<T>::type *__restrict__ xs,
+                                                         const int *__restrict__ ls, const int *__restrict__ perm,
+                                                         int nside, int log2n, T w, int p, int pc,
+                                                         const T *__restrict__ Mu, const T *__restrict__ gamma,
+                                                         T *__restrict__ dgamma, T *__restrict__ dxf)
+{
+    typedef typename C2<T>::type T2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nc = (p + 1) * (p + 1);
+    T *mus = (T *)smem_raw;  // [3][nc] times s_nm
+    const int leaf = blockIdx.x;
+    const int b = ls[leaf], e = ls[leaf + 1];
+    if (e <= b) return;
+    for (int o = threadIdx.x; o < 3 * nc; o += blockDim.x) {
+        const int comp = o / nc, k = o - comp * nc;
+        int n, m, part;
+        unpack_k(k, n, m, part);
+        mus[o] = Mu[(size_t)leaf * 3 * pc + comp * pc + k] * sfac_t<T>(n, m);
+    }
+    __syncthreads();
+    const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
+    const T zx = (cx + T(0.5)) * w, zy = (cy + T(0.5)) * w, zz = (cz + T(0.5)) * w;
+    const T invw = T(1) / w;
+    T2 Y[(PMAX + 1) * (PMAX + 2) / 2];
+    for (int j = b + threadIdx.x; j < e; j += blockDim.x) {
+        const typename V4<T>::type xp = xs[j];
+        y_table<T>((xp.x - zx) * invw, (xp.y - zy) * invw, (xp.z - zz) * invw, p, Y);
+        T phi[3] = {0, 0, 0}, g[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // g[c][b] = d_b Phi_c
+        for (int k = 0; k < nc; ++k) {
+            int n, m, part;
+            unpack_k(k, n, m, part);
+            const T2 yv = Y[cix(n, m)];
+            const T h = part ? yv.y : yv.x;
+            T gx = 0, gy = 0, gz = 0;
+            if (n >= 1) y_grad_part<T>(Y, p, n, m, part, gx, gy, gz);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T mu = mus[c * nc + k];
+                phi[c] += mu * h;
+                g[c][0] += mu * gx;
+                g[c][1] += mu * gy;
+                g[c][2] += mu * gz;
+            }
+        }
+        const int64_t s = perm[j];
+        const T g0 = gamma[3 * s], g1 = gamma[3 * s + 1], g2 = gamma[3 * s + 2];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dgamma[3 * s + c] += phi[c];
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) dxf[3 * s + bb] = invw * (g0 * g[0][bb] + g1 * g[1][bb] + g2 * g[2][bb]);
+    }
+}
+
+// lattice^T and root M2M^T in FP64: mu_0 = Op^T lambda_0; mu_1[b] += M2M_b^T mu_0
+template <typename T>
+__global__ void k_root_lattice_t(const double *__restrict__ op, const T *__restrict__ L0, int nc, int pc,
+                                 double *__restrict__ mu0)
+{
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (o >= 3 * nc) return;
+    const int comp = o / nc, j = o - comp * nc;
+    double s = 0.0;
+    for (int k = lane; k < nc; k += 32) s += op[(size_t)k * nc + j] * (double)L0[comp * pc + k];
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) mu0[o] = s;
+}
+
+template <typename T>
+__global__ void k_root_m2m_t(const double *__restrict__ m2m, const double *__restrict__ mu0, int nc, int pc,
+                             T *__restrict__ M1)
+{
+    const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (o >= 8 * 3 * nc) return;
+    const int bc = o / nc, j = o - bc * nc;  // bc = child * 3 + comp
+    const int child = bc / 3, comp = bc - 3 * child;
+    const double *A = m2m + (size_t)child * nc * nc;
+    double s = 0.0;
+    for (int k = lane; k < nc; k += 32) s += A[(size_t)k * nc + j] * mu0[comp * nc + k];
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) M1[((size_t)child * 3 + comp) * pc + j] += (T)s;
+}
+
+int launch_dual_p2m(Ctx *c, const void *ws_sorted)
+{
+    int log2n = 0;
+    while ((1 << log2n) < c->nside) ++log2n;
+    if (c->pc > DUAL_BS || c->p < 1) {
+        c->last_error = "transposed L2P supports at most 128 padded coefficients";
+        return VFMM_ERR_UNSUPPORTED;
+    }
+    const size_t off = c->lvl_off[c->depth];
+    const int ny = c->p * (c->p + 1) / 2;
+    if (c->f64) {
+        const size_t sm = (size_t)DualCfg<double>::TP * (ny * sizeof(double2) + sizeof(dvec4));
+        k_dual_p2m<double><<<(unsigned)c->nleaf, DUAL_BS, sm, c->stream>>>(
+            (const dvec4 *)c->xs.p, (const dvec4 *)ws_sorted, (const int *)c->leaf_start.p, c->nside, log2n,
+            c->leaf_w, c->p, c->pc, (double *)c->lexp.p + off);
+    } else {
+        const size_t sm = (size_t)DualCfg<float>::TP * (ny * sizeof(float2) + sizeof(float4));
+        k_dual_p2m<float><<<(unsigned)c->nleaf, DUAL_BS, sm, c->stream>>>(
+            (const float4 *)c->xs.p, (const float4 *)ws_sorted, (const int *)c->leaf_start.p, c->nside, log2n,
+            (float)c->leaf_w, c->p, c->pc, (float *)c->lexp.p + off);
+    }
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+int launch_dual_l2p(Ctx *c, const void *gamma, void *dgamma, void *dxf)
+{
+    int log2n = 0;
+    while ((1 << log2n) < c->nside) ++log2n;
+    const size_t off = c->lvl_off[c->depth];
+    const size_t sm = (size_t)3 * c->nc * c->esz;
+    if (c->f64)
+        k_dual_l2p<double><<<(unsigned)c->nleaf, DUAL_L2P_BS, sm, c->stream>>>(
+            (const dvec4 *)c->xs.p, (const int *)c->leaf_start.p, (const int *)c->perm.p, c->nside, log2n,
+            c->leaf_w, c->p, c->pc, (const double *)c->mexp.p + off, (const double *)gamma, (double *)dgamma,
+            (double *)dxf);
+    else
+        k_dual_l2p<float><<<(unsigned)c->nleaf, DUAL_L2P_BS, sm, c->stream>>>(
+            (const float4 *)c->xs.p, (const int *)c->leaf_start.p, (const int *)c->perm.p, c->nside, log2n,
+            (float)c->leaf_w, c->p, c->pc, (const float *)c->mexp.p + off, (const float *)gamma, (float *)dgamma,
+            (float *)dxf);
+    VFMM_CUDA_CHECK_LAUNCH(c);
+    return VFMM_OK;
+}
+
+int launch_root_t(Ctx *c)
+{
+    const int wpb = 8;
+    const unsigned nb1 = (unsigned)((3 * c->nc + wpb - 1) / wpb), nb2 = (unsigned)((24 * c->nc + wpb - 1) / wpb);
+    if (c->f64) {
+        k_root_lattice_t<double><<<nb1, 32 * wpb, 0, c->stream>>>((const double *)c->lattice_f64.p,
+                                                                   (const double *)c->lexp.p, c->nc, c->pc,
+                                                                   (double *)c->root_m.p);
+        VFMM_CUDA_CHECK_LAUNCH(c);
+        k_root_m2m_t<double><<<nb2, 32 * wpb, 0, c->stream>>>((const double *)c->m2m_f64.p,
+                                                               (const double *)c->root_m.p, c->nc, c->pc,
+                                                               (double *)c->mexp.p + c->lvl_off[1]);
+    } else {
+        k_root_lattice_t<float><<<nb1, 32 * wpb, 0, c->stream>>>((const double *)c->lattice_f64.p,
+                                                                  (const float *)c->lexp.p, c->nc, c->pc,
+                                                                  (double *)c->root_m.p);
+        VFMM_CUDA_CHECK_LAUNCH(c);
+        k_root_m2m_t<float><<<nb2, 32 * wpb, 0, c->stream>>>((const double *)c->m2m_f64.p,
+                                                              (const double *)c->root_m.p, c->nc, c->pc,
+                                                              (float *)c->mexp.p + c->lvl_off[1]);
+    }
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
 }

@@ -22,10 +22,15 @@
 // K = 16 bf16 / 8 tf32 per instruction) from shared-memory descriptors in the canonical
 // no-swizzle K-major layout (8-row x 16-byte core matrices); producer warps gather the source
 // rows with cp.async and one producer thread moves the pre-tiled translation matrices with
-// TMA bulk copies (expect_tx); tcgen05.commit arrives on one mbarrier per stage so a stage is
-// refilled only after the MMAs that read it completed.  Every mbarrier wait is bounded: on
-// timeout the kernel sets an error bit, waits (bounded) for its own loads, frees TMEM and
-// returns.
+// TMA bulk copies (expect_tx on a per-stage transaction barrier); tcgen05.commit arrives on one
+// mbarrier per stage so a stage is refilled only after the MMAs that read it completed.
+// Every pipeline wait is bounded (TcParams.wait_limit tries).  A thread that gives up sets a
+// shared abort word, which every other pipeline wait polls, so the whole CTA stops issuing;
+// producer warps decide with one lane and leave their loop together.  Before TMEM is freed
+// the CTA drains its own asynchronous work: each producer thread waits for its cp.async
+// copies, producer thread 0 waits for the last transaction of every stage it filled with bulk
+// copies, and the MMA thread commits once more and waits for that commit (every MMA it issued
+// has then completed).  The kernel then sets the timeout bit of the error word and returns.
 #include "common.cuh"
 #include "vfmm_internal.h"
 
@@ -76,20 +81,59 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 {
-    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Pipeline wait: gives up after `limit` tries, or as soon as another thread of the CTA has given
+// up (the shared abort word); a thread that gives up itself sets the abort word.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit, volatile int *abort)
+{
+    for (long long it = 0; it < limit; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort) return false;
     }
+    *abort = 1;
     return false;
+}
+
+// Drain wait for the CTA's own asynchronous work (bulk copies, MMAs), which completes by itself:
+// not cut short by the abort word, bounded by the fixed limit.
+__device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity)
+{
+    for (long long it = 0; it < TC_WAIT_LIMIT; ++it)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+// Warp-uniform pipeline wait: lane 0 waits, every lane takes its answer (so a warp leaves a loop
+// together and no lane is left at a __syncwarp).
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, long long limit, volatile int *abort)
+{
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, limit, abort) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// Bulk-copy drain of one producer thread: for each stage, wait for the last transaction phase
+// it issued there (stage s had n_s = issues on it; the last completes phase n_s - 1).
+template <int STAGES> __device__ __forceinline__ bool drain_bulk(const uint64_t *tx, int issued)
+{
+    bool ok = true;
+    for (int s = 0; s < STAGES && s < issued; ++s) {
+        const int ns = (issued - s + STAGES - 1) / STAGES;
+        ok = mbar_wait_drain(smem_u32(&tx[s]), (uint32_t)((ns - 1) & 1)) && ok;
+    }
+    return ok;
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
@@ -143,9 +187,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 
 // Warp-specialised pipeline: warp 0 lane 0 issues the MMAs; warps 1..4 (128 producer threads)
 // gather the multipole rows with cp.async and release a stage (fence.proxy.async by every
-// lane, one arrive per warp on full[s]) TC_PF stages after issuing it; producer thread 0 also moves the two pre-tiled
-// translation-matrix tiles with TMA bulk copies (expect_tx on full[s]).  tcgen05.commit on
-// empty[s] returns the slot to the producers.  No CTA-wide barrier inside the main loop.
+// lane, one arrive per warp on full[s]) TC_PF stages after issuing it; producer thread 0 also
+// moves the two pre-tiled translation-matrix tiles with TMA bulk copies (expect_tx on tx[s]).
+// The MMA thread waits for full[s] and tx[s]; tcgen05.commit on empty[s] returns the slot to
+// the producers.  No CTA-wide barrier inside the main loop.
 // Producer release lag.  A stage is released after the producer has issued TC_PF later stages,
 // and issuing stage i waits for the MMAs of stage i - TC_STAGES; TC_STAGES - TC_PF >= 3 keeps an
 // MMA queued behind the running one (a lag of 4 of 5 stages serialised the MMAs).
@@ -160,7 +205,10 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
     unsigned char *stages = base;
     uint64_t *full = (uint64_t *)(base + TC_STAGES * TC_STAGE_BYTES);
     uint64_t *empty = full + TC_STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(empty + TC_STAGES);
+    uint64_t *tx = empty + TC_STAGES;    // bulk-copy bytes of each stage
+    uint64_t *drain = tx + TC_STAGES;    // final tcgen05.commit
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    volatile int *abort = (volatile int *)(tmem_slot + 1);
     int4 *kb_s = (int4 *)(base + TC_STAGES * TC_STAGE_BYTES + 256);
     int *cell_s = (int *)(kb_s + TC_MAXKB);
 
@@ -187,9 +235,12 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_init(smem_u32(&full[s]), TC_THREADS / 32 + 1);  // one arrival per producer warp + expect_tx
+            mbar_init(smem_u32(&full[s]), TC_THREADS / 32);  // one arrival per producer warp
             mbar_init(smem_u32(&empty[s]), 1);              // tcgen05.commit
+            mbar_init(smem_u32(&tx[s]), 1);                 // expect_tx of the bulk copies
         }
+        mbar_init(smem_u32(drain), 1);
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
@@ -212,7 +263,9 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
                                    ((uint32_t)(TC_M >> 4) << 24);
             for (int i = 0; i < nk; ++i) {
                 const int s = i % TC_STAGES;
-                if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((i / TC_STAGES) & 1))) {
+                const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
+                if (!mbar_wait(smem_u32(&full[s]), ph, tp.wait_limit, abort) ||
+                    !mbar_wait(smem_u32(&tx[s]), ph, tp.wait_limit, abort)) {
                     ok = false;
                     break;
                 }
@@ -232,10 +285,14 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
                 }
                 mma_commit(smem_u32(&empty[s]));
             }
+            // drain: every MMA issued above has completed once this commit arrives
+            mma_commit(smem_u32(drain));
+            if (!mbar_wait_drain(smem_u32(drain), 0u)) ok = false;
         }
     } else {
         // ------------------------------- producers ---------------------------------
         const int ptid = tid - 32;
+        int issued = 0;  // stages whose bulk copies producer thread 0 issued
         int slot_cx[TC_BCHUNKS], slot_cy[TC_BCHUNKS], slot_cz[TC_BCHUNKS], slot_comp[TC_BCHUNKS], slot_kg[TC_BCHUNKS];
 #pragma unroll
         for (int j = 0; j < TC_BCHUNKS; ++j) {
@@ -257,19 +314,21 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
             if (i < nk) {
                 const int s = i % TC_STAGES;
                 if (i >= TC_STAGES &&
-                    !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((i / TC_STAGES) - 1) & 1))) {
+                    !mbar_wait_warp(smem_u32(&empty[s]), (uint32_t)(((i / TC_STAGES) - 1) & 1), tp.wait_limit, abort)) {
                     ok = false;
                     break;
                 }
                 int kbi = i / nchunk, ch = i - kbi * nchunk;
                 int4 kb = kb_s[kbi];
+                kb.x = checked_index(kb.x, NT, tp.err);
                 unsigned char *st = stages + s * TC_STAGE_BYTES;
                 uint32_t sA = smem_u32(st), sAl = sA + TC_A_BYTES, sB = sAl + TC_A_BYTES, sBl = sB + TC_B_BYTES;
                 if (ptid == 0) {
-                    uint32_t fb = smem_u32(&full[s]);
+                    uint32_t fb = smem_u32(&tx[s]);
                     mbar_expect_tx(fb, 2 * TC_A_BYTES);
                     bulk_g2s(sA, Ahi + ((size_t)kb.x * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
                     bulk_g2s(sAl, Alo + ((size_t)kb.x * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
+                    issued = i + 1;
                 }
 #pragma unroll
                 for (int j = 0; j < TC_BCHUNKS; ++j) {
@@ -277,7 +336,7 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
                     int sx = (slot_cx[j] + kb.y) & (n - 1);
                     int sy = (slot_cy[j] + kb.z) & (n - 1);
                     int sz = (slot_cz[j] + kb.w) & (n - 1);
-                    int64_t src = ((int64_t)sx * n + sy) * n + sz;
+                    const int64_t src = checked_index<int64_t>(((int64_t)sx * n + sy) * n + sz, (int64_t)n * n * n, tp.err);
                     size_t off = (size_t)(src * 3 + slot_comp[j]) * row_bytes + (size_t)ch * TC_KBYTES + 16 * slot_kg[j];
                     cp_async16(sB + 16 * v, Bhi + off);
                     cp_async16(sBl + 16 * v, Blo + off);
@@ -293,14 +352,13 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
                 if ((tid & 31) == 0) mbar_arrive(smem_u32(&full[(i - TC_PF) % TC_STAGES]));
             }
         }
+        // drain: this thread's cp.async copies, and producer thread 0's bulk copies
         cp_async_wait<0>();
+        if (ptid == 0 && !drain_bulk<TC_STAGES>(tx, issued)) ok = false;
     }
-    // epilogue: wait for the last MMAs (bounded), then warps 0..3 read TMEM lanes 32w..32w+31
-    if (ok && nk > 0 && warp < 4) {
-        int li = nk - 1;
-        ok = mbar_wait(smem_u32(&empty[li % TC_STAGES]), (uint32_t)((li / TC_STAGES) & 1));
-    }
-    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    // epilogue: the MMA thread has seen its drain commit arrive (all MMAs done) before this
+    // barrier; then warps 0..3 read TMEM lanes 32w..32w+31
+    ok = __syncthreads_and((ok && !*abort) ? 1 : 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok && warp < 4) {
         const int k = 32 * warp + (tid & 31);
@@ -323,7 +381,7 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
                 C[((int64_t)cell_s[q] * 3 + comp) * pc + k] = __uint_as_float(r[e]);
             }
         }
-    } else if (!ok && tid == 0) {
+    } else if (tid == 0) {
         atomicOr(tp.err, ERRBIT_TIMEOUT);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -389,7 +447,10 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
     unsigned char *stages = base;
     uint64_t *full = (uint64_t *)(base + TL_STAGES * Gm::STAGE);
     uint64_t *empty = full + TL_STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(empty + TL_STAGES);
+    uint64_t *tx = empty + TL_STAGES;    // bulk-copy bytes of each stage
+    uint64_t *drain = tx + TL_STAGES;    // final tcgen05.commit
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    volatile int *abort = (volatile int *)(tmem_slot + 1);
     int4 *cls_s = (int4 *)(base + TL_STAGES * Gm::STAGE + 256);
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -404,9 +465,12 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
 
     if (tid == 0) {
         for (int s = 0; s < TL_STAGES; ++s) {
-            mbar_init(smem_u32(&full[s]), TC_THREADS / 32 + 1);  // one arrival per producer warp + expect_tx
-            mbar_init(smem_u32(&empty[s]), 1);                  // tcgen05.commit
+            mbar_init(smem_u32(&full[s]), TC_THREADS / 32);  // one arrival per producer warp
+            mbar_init(smem_u32(&empty[s]), 1);              // tcgen05.commit
+            mbar_init(smem_u32(&tx[s]), 1);                 // expect_tx of the bulk copies
         }
+        mbar_init(smem_u32(drain), 1);
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
@@ -429,7 +493,9 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
                                    ((uint32_t)(TC_M >> 4) << 24);
             for (int i = 0; i < nk; ++i) {
                 const int s = i % TL_STAGES;
-                if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((i / TL_STAGES) & 1))) {
+                const uint32_t ph = (uint32_t)((i / TL_STAGES) & 1);
+                if (!mbar_wait(smem_u32(&full[s]), ph, tp.wait_limit, abort) ||
+                    !mbar_wait(smem_u32(&tx[s]), ph, tp.wait_limit, abort)) {
                     ok = false;
                     break;
                 }
@@ -458,17 +524,21 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
                 }
                 mma_commit(smem_u32(&empty[s]));
             }
+            // drain: every MMA issued above has completed once this commit arrives
+            mma_commit(smem_u32(drain));
+            if (!mbar_wait_drain(smem_u32(drain), 0u)) ok = false;
         }
     } else {
         // ------------------------------- producers ---------------------------------
         const int ptid = tid - 32;
+        int issued = 0;  // stages whose bulk copies producer thread 0 issued
         const unsigned char *Ahi = (const unsigned char *)tp.Ahi, *Alo = (const unsigned char *)tp.Alo;
         const unsigned char *Bhi = (const unsigned char *)tp.Bhi, *Blo = (const unsigned char *)tp.Blo;
         for (int i = 0; i < nk + TL_PF; ++i) {
             if (i < nk) {
                 const int s = i % TL_STAGES;
                 if (i >= TL_STAGES &&
-                    !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((i / TL_STAGES) - 1) & 1))) {
+                    !mbar_wait_warp(smem_u32(&empty[s]), (uint32_t)(((i / TL_STAGES) - 1) & 1), tp.wait_limit, abort)) {
                     ok = false;
                     break;
                 }
@@ -477,10 +547,11 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
                 const int cnt = min(hd.w, TL_MAXOFF);
                 const uint32_t st = smem_u32(stages + s * Gm::STAGE);
                 if (ptid == 0) {
-                    const uint32_t fb = smem_u32(&full[s]);
+                    const uint32_t fb = smem_u32(&tx[s]);
+                    issued = i + 1;
                     mbar_expect_tx(fb, (uint32_t)(cnt * 2 * TC_A_BYTES));
                     for (int e = 0; e < cnt; ++e) {
-                        const int tile = e == 0 ? e01.x : e == 1 ? e01.z : e23.x;
+                        const int tile = checked_index(e == 0 ? e01.x : e == 1 ? e01.z : e23.x, NT, tp.err);
                         const uint32_t sA = st + (uint32_t)(e * 2 * TC_A_BYTES);
                         bulk_g2s(sA, Ahi + ((size_t)tile * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
                         bulk_g2s(sA + TC_A_BYTES, Alo + ((size_t)tile * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
@@ -498,7 +569,9 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
                     const int L = line0 + l;
                     const int px = L / H, py = L - (L / H) * H;
                     const int X = (px + shx) & (H - 1), Y = (py + shy) & (H - 1);
-                    const size_t srow = (((size_t)(ch * 8 + bpar) * H + X) * H + Y) * Gm::ROWS_LINE + zp * 3 + comp;
+                    const int64_t srow = checked_index<int64_t>(
+                        (((int64_t)(ch * 8 + bpar) * H + X) * H + Y) * Gm::ROWS_LINE + zp * 3 + comp,
+                        (int64_t)nchunk * 8 * H * H * Gm::ROWS_LINE, tp.err);
                     const size_t off = srow * TC_KBYTES + 16 * kg;
                     const uint32_t dst = (uint32_t)(kg * Gm::PLANE + r * 16);
                     cp_async16(sB + dst, Bhi + off);
@@ -513,14 +586,13 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
                 if ((tid & 31) == 0) mbar_arrive(smem_u32(&full[(i - TL_PF) % TL_STAGES]));
             }
         }
+        // drain: this thread's cp.async copies, and producer thread 0's bulk copies
         cp_async_wait<0>();
+        if (ptid == 0 && !drain_bulk<TL_STAGES>(tx, issued)) ok = false;
     }
-    // epilogue: wait for the last MMAs (bounded), then warps 0..3 read TMEM lanes 32w..32w+31
-    if (ok && nk > 0 && warp < 4) {
-        int li = nk - 1;
-        ok = mbar_wait(smem_u32(&empty[li % TL_STAGES]), (uint32_t)((li / TL_STAGES) & 1));
-    }
-    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    // epilogue: the MMA thread has seen its drain commit arrive (all MMAs done) before this
+    // barrier; then warps 0..3 read TMEM lanes 32w..32w+31
+    ok = __syncthreads_and((ok && !*abort) ? 1 : 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok && warp < 4) {
         const int k = 32 * warp + (tid & 31);
@@ -548,7 +620,7 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
                 C[(cell * 3 + comp) * pc + k] = __uint_as_float(r[e]);
             }
         }
-    } else if (!ok && tid == 0) {
+    } else if (tid == 0) {
         atomicOr(tp.err, ERRBIT_TIMEOUT);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -762,6 +834,7 @@ int launch_tc_m2l(Ctx *c, int level, int R, bool bf16)
     tp.pc = c->pc;
     tp.nchunk = c->pc * (bf16 ? 2 : 4) / TC_KBYTES;
     tp.err = (int *)c->err.p;
+    tp.wait_limit = c->wait_limit;
     if (grid_level(level)) {
         const int h = n / 2;
         if (h == 16) return bf16 ? launch_lines<true, 16>(c, level, R, tp) : launch_lines<false, 16>(c, level, R, tp);

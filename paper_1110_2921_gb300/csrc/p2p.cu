@@ -143,17 +143,45 @@ struct P3Const {
     float d2_cut;      // (rho_cut sigma)^2: beyond the near rings, octants closer than this are corrected
     float w2_lo;       // leaf width squared, less a rounding margin
     float L;
-    float as[5];       // A&S 7.1.26 coefficients a1..a5
 };
 
-#ifndef VFMM_P3_CPOLY
-#define VFMM_P3_CPOLY 1
+// In the scaled coordinates sigma s = sqrt(log2(e) / 2) whatever sigma is, so every constant of
+// the pair arithmetic is a fixed number.  The erf polynomial's coefficients are compiled in as
+// immediates (2.5 % faster than reading them from the kernel parameters at 256^3);
+// VFMM_P3_IMM=1 compiles the sigma-derived constants in as well (measured 0.3 % slower).
+constexpr double P3_SS = 0.84932180028801904272;  // sigma s = sqrt(log2(e) / 2)
+constexpr double P3_CPI = 0.79788456080286535588;  // sqrt(2 / pi)
+constexpr float P3_CT = (float)(0.3275911 / (1.41421356237309504880 * P3_SS));
+constexpr float P3_CQ = (float)(P3_CPI / P3_SS);
+constexpr float P3_CF = (float)(P3_CPI / (P3_SS * P3_SS * P3_SS));
+constexpr float P3_R2S = (float)(0.25 * P3_SS * P3_SS);
+constexpr float P3_INV_S2 = (float)(1.0 / (P3_SS * P3_SS));
+constexpr float P3_FS = (float)(P3_CPI / (P3_SS * P3_SS * P3_SS * P3_SS * P3_SS));
+
+#ifndef VFMM_P3_IMM
+#define VFMM_P3_IMM 0
 #endif
+#if VFMM_P3_IMM
+#define P3K_CT P3_CT
+#define P3K_CQ P3_CQ
+#define P3K_CF P3_CF
+#define P3K_R2S P3_R2S
+#define P3K_INV_S2 P3_INV_S2
+#define P3K_KS P3_CF
+#define P3K_FS P3_FS
+#else
+#define P3K_CT k.ct
+#define P3K_CQ k.cq
+#define P3K_CF k.cf
+#define P3K_R2S k.r2s
+#define P3K_INV_S2 k.inv_s2
+#define P3K_KS k.ks
+#define P3K_FS k.fs
+#endif
+
 // t P(t) of A&S 7.1.26: erfc(x) = t P(t) exp(-x^2), t = 1/(1 + p x)
-__device__ __forceinline__ float as_poly(const P3Const &k, float t)
+__device__ __forceinline__ float as_poly(const P3Const &, float t)
 {
-    if (VFMM_P3_CPOLY)
-        return t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, k.as[4], k.as[3]), k.as[2]), k.as[1]), k.as[0]);
     return t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
                     0.254829592f);
 }
@@ -173,12 +201,12 @@ __device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, fl
         float e = ex2_approx(-r2);
         float rinv = rsqrt_approx(r2);
         float r = r2 * rinv;
-        float t = rcp_approx(fmaf(r, k.ct, 1.0f));
+        float t = rcp_approx(fmaf(r, P3K_CT, 1.0f));
         float poly = as_poly(k, t);
-        float omq = e * fmaf(k.cq, r, poly);  // 1 - q(rho)
+        float omq = e * fmaf(P3K_CQ, r, poly);  // 1 - q(rho)
         float rinv2 = rinv * rinv;
         K = -omq * (rinv2 * rinv);
-        F = rinv2 * fmaf(-3.0f, K, k.cf * e);
+        F = rinv2 * fmaf(-3.0f, K, P3K_CF * e);
     } else if (MODE == 2) {  // singular kernel: K = 1/r^3, F = -3/r^5
         float rinv = rsqrt_approx(r2);
         float rinv2 = rinv * rinv;
@@ -188,17 +216,17 @@ __device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, fl
         float e = ex2_approx(-r2);
         float rinv = rsqrt_approx(r2);
         float r = r2 * rinv;
-        float t = rcp_approx(fmaf(r, k.ct, 1.0f));
+        float t = rcp_approx(fmaf(r, P3K_CT, 1.0f));
         float poly = as_poly(k, t);
-        float q = fmaf(-e, fmaf(k.cq, r, poly), 1.0f);
+        float q = fmaf(-e, fmaf(P3K_CQ, r, poly), 1.0f);
         float rinv2 = rinv * rinv;
         K = q * (rinv2 * rinv);
-        F = rinv2 * fmaf(-3.0f, K, k.cf * e);
+        F = rinv2 * fmaf(-3.0f, K, P3K_CF * e);
         if (MODE == 0) {
-            if (r2 < k.r2s) {  // rho < 0.5, including the self pair
-                float x = r2 * k.inv_s2;
-                K = k.ks * series_k<float>(x);
-                F = k.fs * series_f<float>(x);
+            if (r2 < P3K_R2S) {  // rho < 0.5, including the self pair
+                float x = r2 * P3K_INV_S2;
+                K = P3K_KS * series_k<float>(x);
+                F = P3K_FS * series_f<float>(x);
             }
         }
     }
@@ -333,7 +361,7 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
                                                         int R, int Rc, int direct_K, float leaf_w, P3Const kc,
                                                         const float *__restrict__ ufar, const float *__restrict__ sfar,
                                                         const int *__restrict__ perm, float *__restrict__ u_out,
-                                                        float *__restrict__ s_out)
+                                                        float *__restrict__ s_out, int *__restrict__ err)
 {
     __shared__ Src3 src[P3_TILE];
     __shared__ int ost[9];
@@ -386,6 +414,7 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
                     }
                     int nx = cx + ox, ny = cy + oy, nz = cz + oz;
                     int sl = ((nx & (nside - 1)) * nside + (ny & (nside - 1))) * nside + (nz & (nside - 1));
+                    sl = checked_index(sl, nside * nside * nside, err);
                     float shx = kc.L * (float)(nx >> log2n), shy = kc.L * (float)(ny >> log2n), shz = kc.L * (float)(nz >> log2n);
                     // closest approach of the target leaf box and each source octant box selects
                     // the inner loop for that octant (warp-uniform): in the near rings smoothed
@@ -565,11 +594,6 @@ int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void
         kc.d2_singular = (float)(42.25 * sigma * sigma);   // (6.5 sigma)^2
         kc.d2_cut = (float)(c->cfg.rho_cut * c->cfg.rho_cut * sigma * sigma);
         kc.w2_lo = (float)(c->leaf_w * c->leaf_w * (1.0 - 1e-4));
-        kc.as[0] = 0.254829592f;
-        kc.as[1] = -0.284496736f;
-        kc.as[2] = 1.421413741f;
-        kc.as[3] = -1.453152027f;
-        kc.as[4] = 1.061405429f;
         kc.L = (float)c->cfg.box;
         int chunks3 = (c->max_leaf + P3_TARGETS - 1) / P3_TARGETS;
         if (chunks3 < 1) chunks3 = 1;
@@ -580,7 +604,7 @@ int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void
                                                        (const int *)c->oct_start.p, (const float4 *)c->oct_box.p,
                                                        c->nside, log2n, R, Rc, direct_K, (float)c->leaf_w, kc,
                                                        (const float *)ufar, (const float *)sfar, (const int *)c->perm.p,
-                                                       (float *)u_out, (float *)s_out);
+                                                       (float *)u_out, (float *)s_out, (int *)c->err.p);
     }
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
@@ -680,12 +704,20 @@ extern "C" int vfmm_direct_eval_noalloc(int64_t n, const float *x, const float *
         cudaGetLastError();
         return VFMM_ERR_CUDA;
     }
-    float4 *scratch;
+    float4 *scratch = nullptr;
     {
-        // one-time set-up per device: the host-side symbol is only a stand-in, so look up the
-        // array's device address with that device current
+        // the host-side symbol is only a stand-in: look up the array's device address with the
+        // device current.  Outside stream capture every call looks it up again (a host-side
+        // table lookup that allocates nothing), so the address follows a module reload after
+        // cudaDeviceReset; during capture the address of the last call outside capture is used.
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+            cudaGetLastError();
+            return VFMM_ERR_CUDA;
+        }
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone || !g_noalloc_ptr[dev]) {
             void *p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {
@@ -890,26 +922,30 @@ int launch_p2p_grad(Ctx *c, int R, double sigma, const void *ufar, const void *g
 // dx_m = G1_m^T w_m + G2_m^T gamma_m (all arrays in caller order)
 template <typename T>
 __global__ void k_adjoint_combine(int64_t n, const T *__restrict__ G1, const T *__restrict__ w,
-                                  const T *__restrict__ G2, const T *__restrict__ g, T *__restrict__ dx)
+                                  const T *__restrict__ G2, const T *__restrict__ g, const T *__restrict__ extra,
+                                  T *__restrict__ dx)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int k = 0; k < 3; ++k) {
-        T s = 0;
+        T s = extra ? extra[3 * i + k] : T(0);
         for (int a = 0; a < 3; ++a) s += G1[9 * i + 3 * a + k] * w[3 * i + a] + G2[9 * i + 3 * a + k] * g[3 * i + a];
         dx[3 * i + k] = s;
     }
 }
 
-int launch_adjoint_combine(Ctx *c, const void *G1, const void *w, const void *G2, const void *gamma, void *dx)
+int launch_adjoint_combine(Ctx *c, const void *G1, const void *w, const void *G2, const void *gamma, const void *extra,
+                           void *dx)
 {
     int nb = (int)((c->n + 255) / 256);
     if (c->f64)
         k_adjoint_combine<double><<<nb, 256, 0, c->stream>>>(c->n, (const double *)G1, (const double *)w,
-                                                            (const double *)G2, (const double *)gamma, (double *)dx);
+                                                            (const double *)G2, (const double *)gamma,
+                                                            (const double *)extra, (double *)dx);
     else
         k_adjoint_combine<float><<<nb, 256, 0, c->stream>>>(c->n, (const float *)G1, (const float *)w,
-                                                           (const float *)G2, (const float *)gamma, (float *)dx);
+                                                           (const float *)G2, (const float *)gamma,
+                                                           (const float *)extra, (float *)dx);
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
 }

@@ -14,7 +14,7 @@ namespace vfmm {
 
 template <typename TIn>
 __global__ void k_keys(int64_t n, const TIn *__restrict__ x, int nside, double L, int *__restrict__ keys,
-                       int *__restrict__ counts)
+                       int *__restrict__ counts, int *__restrict__ err)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < n;
@@ -23,13 +23,18 @@ __global__ void k_keys(int64_t n, const TIn *__restrict__ x, int nside, double L
         // coordinates in the input's own precision (FP64 arithmetic is scarce on this part)
         const TIn Lt = (TIn)L, invL = (TIn)(1.0 / L), scale = (TIn)((double)nside / L);
         int c[3];
+        bool finite = true;
         for (int d = 0; d < 3; ++d) {
+            finite = finite && isfinite(x[3 * i + d]);
             TIn v = wrap_coord<TIn>(x[3 * i + d], Lt, invL);
             int ci = (int)(v * scale);
             c[d] = ci < 0 ? 0 : (ci >= nside ? nside - 1 : ci);
         }
         key = (c[0] * nside + c[1]) * nside + c[2];
         keys[i] = key;
+        // a NaN or infinite coordinate has no leaf: the clamped key keeps every access in bounds
+        // and the error bit makes vfmm_build_tree fail with VFMM_ERR_ARG
+        if (!finite) atomicOr(err, ERRBIT_NONFINITE);
     }
     // one atomic per run of equal keys in the warp (neighbouring particles share leaves):
     // the first lane of a run adds the run length
@@ -262,7 +267,8 @@ template <typename TIn, typename T> static int tree_impl(Ctx *c, const TIn *x)
     cudaMemsetAsync(c->fill.p, 0, nleaf * sizeof(int), st);
     cudaMemsetAsync(c->maxleaf.p, 0, sizeof(int), st);
     int nb = (int)((n + 255) / 256);
-    k_keys<TIn><<<nb, 256, 0, st>>>(n, x, c->nside, c->cfg.box, (int *)c->keys.p, (int *)c->counts.p);
+    k_keys<TIn><<<nb, 256, 0, st>>>(n, x, c->nside, c->cfg.box, (int *)c->keys.p, (int *)c->counts.p,
+                                        (int *)c->err.p);
     int nparts = (int)((nleaf + 1023) / 1024);
     int *start = (int *)c->leaf_start.p;
     int *part = (int *)c->scan_part.p;

@@ -25,6 +25,30 @@ constexpr int TC_A_TILE = 128 * TC_KBYTES;  // bytes of one translation-matrix t
 constexpr int ERRBIT_LEAF_OVERFLOW = 1;
 constexpr int ERRBIT_BOUNDS = 2;
 constexpr int ERRBIT_TIMEOUT = 4;
+constexpr int ERRBIT_NONFINITE = 8;  // a position given to the tree build is NaN or infinite
+
+// Checked build (-DVFMM_CHECK=1): the gather indices of the M2L/M2M/L2L GEMM, the tensor-core
+// M2L and the P2P are range-checked; an index out of range sets ERRBIT_BOUNDS and is replaced
+// by 0, so the access stays in bounds and the evaluation reports VFMM_ERR_BOUNDS.  The default
+// build checks nothing (every index is in range by construction).
+#ifndef VFMM_CHECK
+#define VFMM_CHECK 0
+#endif
+#ifdef __CUDACC__
+template <typename I> __device__ __forceinline__ I checked_index(I idx, I limit, int *err)
+{
+#if VFMM_CHECK
+    if (idx < 0 || idx >= limit) {
+        atomicOr(err, ERRBIT_BOUNDS);
+        return 0;
+    }
+#else
+    (void)limit;
+    (void)err;
+#endif
+    return idx;
+}
+#endif
 
 namespace ops {
 double sfac(int n, int m);
@@ -56,6 +80,7 @@ struct GemmParams {
     int pc;           // padded coefficient stride (multiple of 16)
     int ksplit;       // k-block slices summed by a second pass (1 = none); set by launch_gemm
     void *partial;    // [ksplit][n_tgt^3][3][pc] slice results when ksplit > 1
+    int *err;         // device error word (bounds bit of the checked build); set by launch_gemm
 };
 
 struct TcParams {
@@ -70,6 +95,7 @@ struct TcParams {
     int *err;               // device error word
     int ksplit;             // offset slices (blockIdx.z) summed by a second pass (1 = none)
     float *partial;         // [ksplit][n^3][3][pc] slice results when ksplit > 1
+    long long wait_limit;   // tries of each pipeline mbarrier wait before the CTA gives up
 };
 
 struct Ctx {
@@ -104,6 +130,11 @@ struct Ctx {
     DevBuf rg_om, rg_r, rg_d, rg_q, rg_t1, rg_t2, rg_dots;  // reinitialisation temporaries
     int depth_override = -1;       // tree depth forced by vfmm_reinit
     DevBuf at_m2l, at_m2m, at_l2l; // CUDA-core matrices, T
+    // transposed operators of the adjoint (built on its first FMM call): at_m2l_t[t] = M2L(-t)^T,
+    // at_l2l_t[b] = L2L_b^T (applied child -> parent), at_m2m_t[b] = M2M_b^T (parent -> child),
+    // and the tensor-core tiles of at_m2l_t
+    DevBuf at_m2l_t, at_m2m_t, at_l2l_t, tc_hi_t, tc_lo_t;
+    bool have_transposed = false;
     DevBuf tc_hi, tc_lo;           // tensor-core tiles
     DevBuf m2m_f64, lattice_f64;   // root accumulation and lattice operator, FP64
     DevBuf root_m;                 // FP64 root multipole
@@ -123,6 +154,7 @@ struct Ctx {
     bool have_events = false;
     bool timed_eval = false;
     int64_t launches = 0;      // kernels launched by the last build + evaluation
+    long long wait_limit = 1LL << 26;  // tries of each tensor-core pipeline wait (vfmm_set_wait_limit)
     double timings[NPHASE];
     std::string last_error;
 };
@@ -135,6 +167,11 @@ int launch_p2m(Ctx *c);
 int launch_gemm(Ctx *c, const GemmParams &gp, int ngroups, int64_t ncell_group);
 int launch_root(Ctx *c);
 int launch_l2p(Ctx *c, bool grad);
+// transposed far field: E^T (w sorted as V4 -> leaf lambda in lexp), P^T (+ source-position term,
+// caller order; dgamma accumulated, dxf written), lattice^T + root M2M^T (lexp level 0 -> mexp level 1)
+int launch_dual_p2m(Ctx *c, const void *ws_sorted);
+int launch_dual_l2p(Ctx *c, const void *gamma, void *dgamma, void *dxf);
+int launch_root_t(Ctx *c);
 // u_out[perm[i]] += ufar[i], s_out[perm[i]] += sfar[i] (FP32)
 int launch_add_far(Ctx *c, void *u_out, void *s_out);
 // energy spectrum of an n^3 x 3 lattice velocity into E_dev[0..kmax] (work: 3 n^3 double2)
@@ -143,7 +180,9 @@ int launch_spectrum(Ctx *c, int n, const void *u, int kmax, double2 *work, doubl
 int launch_moments(Ctx *c, int64_t n, const void *g, double *out_dev);
 int launch_p2p_grad(Ctx *c, int R, double sigma, const void *ufar, const void *gfar, void *u_out, void *g_out,
                     int direct_K);
-int launch_adjoint_combine(Ctx *c, const void *G1, const void *w, const void *G2, const void *gamma, void *dx);
+// dx = G1^T w + G2^T gamma (+ extra when not null), caller order
+int launch_adjoint_combine(Ctx *c, const void *G1, const void *w, const void *G2, const void *gamma, const void *extra,
+                           void *dx);
 // direct_K >= 0: direct sum over every leaf of the (2K+1)^3 image boxes; -1: the FMM near field (R rings)
 int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void *sfar, void *u_out,
                void *s_out, int direct_K);

@@ -41,8 +41,13 @@ def test_host_only_calls():
     assert nv.lib().vfmm_create(ctypes.byref(bad), ctypes.byref(h)) == nv.VFMM_ERR_ARG
     assert nv.lib().vfmm_build_tree(None, 10, None) == nv.VFMM_ERR_ARG
     assert nv.lib().vfmm_sync(None) == nv.VFMM_ERR_ARG
+    assert nv.lib().vfmm_set_wait_limit(None, 5) == nv.VFMM_ERR_ARG
     assert nv.lib().vfmm_energy_spectrum(None, 16, None, 8, None) == nv.VFMM_ERR_ARG
     assert nv.lib().vfmm_derivative_moments(None, 10, None, None) == nv.VFMM_ERR_ARG
+    ops = ctypes.c_double(0.0)
+    # argument checks of the peak probes come before any CUDA call
+    assert nv.lib().vfmm_probe_peak(nv.VFMM_PROBE_FFMA, 0, None, None, ctypes.byref(ops)) == nv.VFMM_ERR_ARG
+    assert nv.lib().vfmm_probe_peak(nv.VFMM_PROBE_FFMA, 10, None, None, None) == nv.VFMM_ERR_ARG
     assert cfg.concurrent_far == 1 and abs(cfg.rho_cut - 5.0) < 1e-15
 
 

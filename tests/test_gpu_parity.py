@@ -150,6 +150,21 @@ def test_errors_reported():
         with pytest.raises(vf.VfmmError) as e:
             h.eval(g, float("nan"))
         assert e.value.status == -1
+        # a NaN or infinite position has no leaf: the tree build fails with VFMM_ERR_ARG, the
+        # handle holds no tree, and a valid build afterwards works
+        for bad in (float("nan"), float("inf"), -float("inf")):
+            xb = x.clone()
+            xb[3, 1] = bad
+            with pytest.raises(vf.VfmmError) as e:
+                h.build_tree(xb)
+            assert e.value.status == -1
+            with pytest.raises(vf.VfmmError) as e:
+                h.eval(g, 0.1)
+            assert e.value.status == -4
+        h.build_tree(x)
+        u, s = h.eval(g, 0.1)
+        h.sync()
+        assert bool(torch.isfinite(u).all())
         # a core so wide that rho_cut sigma exceeds two leaf widths: the near field would need
         # a third ring
         xx = torch.rand(4096, 3, device="cuda") * 6.28

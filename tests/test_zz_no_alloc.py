@@ -1,8 +1,9 @@
 """vfmm_direct_eval_noalloc: the direct sum for callers that cannot allocate device memory
 when they call in (a program that gives all device memory to its own pool, or a loop that
 must not pay cudaMalloc's implicit synchronisation).  Its scratch lives in a static device
-array; this test checks it against the handle-based direct sum (VFMM_METHOD_DIRECT, FP32) on
-two calls in a row, the second with a smaller n so stale scratch from the first would show.
+array; this test checks it against the FP64 oracle's direct sum over the central 27 boxes and
+against the handle-based direct sum (VFMM_METHOD_DIRECT, FP32) on two calls in a row, the
+second with a smaller n so stale scratch from the first would show.
 
 The file name sorts last so a run that stops at the first failure has run everything else.
 """
@@ -11,6 +12,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import workload as wl
 from gpu_util import rel_l2, run_fmm, torch_cuda
 
@@ -34,7 +36,7 @@ def _noalloc(lib, torch, x, g, sigma, images=1):
     return rc, U.double().cpu().numpy(), S.double().cpu().numpy()
 
 
-def test_noalloc_direct_matches_handle_direct_twice():
+def test_noalloc_direct_matches_oracle_and_handle_direct_twice():
     torch = torch_cuda()
     from paper_1110_2921_gb300 import _native
     lib = _native.lib()
@@ -44,6 +46,9 @@ def test_noalloc_direct_matches_handle_direct_twice():
     for x, g in cases:
         rc, u, s = _noalloc(lib, torch, x, g, f["sigma"])
         assert rc == 0
+        uo, so = oracle.direct(x, g, f["sigma"], K=1)
+        assert rel_l2(u, uo) < TOL
+        assert rel_l2(s, so) < TOL
         ur, sr, _ = run_fmm(x, g, f["sigma"], method="direct", direct_images=1, dtype="f32")
         assert rel_l2(u, ur) < TOL
         assert rel_l2(s, sr) < TOL
