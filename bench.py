@@ -363,6 +363,15 @@ def run_timestep(args):
         e1.record()
         torch.cuda.synchronize()
         step_ms = e0.elapsed_time(e1) / 10
+        # where one evaluation at the final core size goes: phases and the P2P's pair count
+        Xs = X.clone()
+        h.build_tree(Xs)
+        h.eval(G, sigma)
+        h.sync()
+        phases = {k: round(v, 3) for k, v in h.timings().items()}
+        info = h.tree_info()
+        pairs, _ = p2p_work(X.double().cpu().numpy(), 2 * math.pi, info["depth"], info["near_rings"], sigma,
+                            info["correction_rings"], args.rho_cut)
         r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         r0.record()
         xn, gn, res = h.reinit(X, G, sigma, n, iters=20)
@@ -371,6 +380,11 @@ def run_timestep(args):
         d1 = h.diagnostics(xn, gn)
         h.close()
         out["runs"][m2l] = {"ms_per_heun_step": step_ms, "particles_per_s": N / (step_ms / 1e3),
+                            "eval_at_final_sigma": {"phases_ms": phases, "depth": info["depth"],
+                                                    "near_rings": info["near_rings"],
+                                                    "correction_rings": info["correction_rings"],
+                                                    "p2p_pairs_per_target": pairs / N,
+                                                    "sigma_over_h": sigma / (2 * math.pi / n)},
                             "ms_reinit": r0.elapsed_time(r1), "reinit_residual": res, "sigma_final": sigma,
                             "total_vorticity_before": d0["total_vorticity"],
                             "total_vorticity_after_reinit": d1["total_vorticity"],

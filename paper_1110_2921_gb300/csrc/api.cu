@@ -419,11 +419,15 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
     // FP32 velocity / stretching: the far field runs on a high-priority side stream while the
     // P2P (near field only) runs on the caller's stream; a last kernel adds the far field
     const bool overlap = fmm && !grad && !c->f64 && c->overlap && c->side;
-    if (overlap) {
+    // fork onto the side stream; with VFMM_FORK_AT_M2L the upward pass (P2M, M2M, root: FP32
+    // ALU work like the P2P's) runs in line first and only the M2L (tensor cores) and the
+    // downward pass run beside the P2P
+    auto fork = [&]() {
         cudaEventRecord(c->ev[11], main_st);
         cudaStreamWaitEvent(c->side, c->ev[11], 0);
         c->stream = c->side;
-    }
+    };
+    if (overlap && !VFMM_FORK_AT_M2L) fork();
     cudaStream_t st = c->stream;
     struct Restore {
         Ctx *c;
@@ -459,6 +463,10 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
             if ((rc = launch_root(c))) return rc;
         }
         cudaEventRecord(c->ev[5], st);
+        if (overlap && VFMM_FORK_AT_M2L) {
+            fork();
+            st = c->stream;
+        }
         const bool tc = c->cfg.m2l_prec == VFMM_M2L_TF32X3 || c->cfg.m2l_prec == VFMM_M2L_BF16X3;
         for (int l = 1; l <= D; ++l) {
             int Rl = (l == D) ? R : 1;
@@ -518,7 +526,10 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
     if (grad) {
         if ((rc = launch_p2p_grad(c, R, sigma, uf, sf, u_out, s_out, fmm ? -1 : c->cfg.direct_images))) return rc;
     } else if (overlap) {
-        if ((rc = launch_p2p(c, R, Rc, sigma, nullptr, nullptr, u_out, s_out, -1))) return rc;
+        c->p2p_shared_blocks = VFMM_P2P_SHARED_BLOCKS;
+        rc = launch_p2p(c, R, Rc, sigma, nullptr, nullptr, u_out, s_out, -1);
+        c->p2p_shared_blocks = 0;
+        if (rc) return rc;
     } else {
         if ((rc = launch_p2p(c, R, Rc, sigma, uf, sf, u_out, s_out, fmm ? -1 : c->cfg.direct_images))) return rc;
     }
@@ -677,6 +688,13 @@ int vfmm_create(const vfmm_config *cfg, vfmm_handle *out)
         }
     }
     c->have_events = true;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            c->sm_count = sms;
+        cudaGetLastError();
+    }
     {
         int lo = 0, hi = 0;
         if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||

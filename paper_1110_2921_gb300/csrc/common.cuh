@@ -34,6 +34,15 @@ template <typename T> __device__ __forceinline__ T wrap_coord(T x, T L, T invL)
 }
 
 __device__ __forceinline__ int imod_pow2(int v, int n) { return v & (n - 1); }
+
+// An SM runs blocks of one shared-memory / L1 split at a time, so kernels that are meant to
+// share SMs (the near-field P2P beside the far-field kernels) all ask for the largest shared
+// carveout; otherwise an SM holding blocks of one split must drain before it takes the other.
+template <typename K> inline void prefer_max_shared(K kernel)
+{
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    cudaGetLastError();
+}
 __device__ __forceinline__ int floordiv_pow2(int v, int log2n) { return v >> log2n; }
 
 }  // namespace vfmm

@@ -57,6 +57,9 @@ void set_constants(int)
     cudaMemcpyToSymbol(c_inv2m_f, i2f, sizeof(i2f));
     cudaMemcpyToSymbol(c_inv2m_d, i2d, sizeof(i2d));
     set_l2p_tables();
+    set_carveouts_expansions();
+    set_carveouts_p2p();
+    set_carveouts_m2l();
 }
 
 __device__ __forceinline__ int pk(int n, int m) { return m == 0 ? n * n : n * n + 2 * m - 1; }
@@ -1143,6 +1146,29 @@ int launch_root_t(Ctx *c)
     }
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
+}
+
+}  // namespace vfmm
+
+namespace vfmm {
+
+void set_carveouts_expansions()
+{
+    prefer_max_shared(k_gather_gamma<float>);
+    prefer_max_shared(k_gather_gamma<double>);
+    prefer_max_shared(k_p2m<float>);
+    prefer_max_shared(k_p2m<double>);
+    prefer_max_shared(k_gemm<float>);
+    prefer_max_shared(k_gemm<double>);
+    prefer_max_shared(k_split_reduce<float>);
+    prefer_max_shared(k_split_reduce<double>);
+    prefer_max_shared(k_root_m2m<float>);
+    prefer_max_shared(k_root_m2m<double>);
+    prefer_max_shared(k_root_lattice<float>);
+    prefer_max_shared(k_root_lattice<double>);
+    prefer_max_shared(k_l2p<float, VFMM_L2P_PP>);
+    prefer_max_shared(k_l2p<double, 1>);
+    prefer_max_shared(k_add_far);
 }
 
 }  // namespace vfmm

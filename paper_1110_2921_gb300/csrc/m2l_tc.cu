@@ -28,8 +28,9 @@
 // shared abort word, which every other pipeline wait polls, so the whole CTA stops issuing;
 // producer warps decide with one lane and leave their loop together.  Before TMEM is freed
 // the CTA drains its own asynchronous work: each producer thread waits for its cp.async
-// copies, producer thread 0 waits for the last transaction of every stage it filled with bulk
-// copies, and the MMA thread commits once more and waits for that commit (every MMA it issued
+// copies; every producer warp arrives on the stages producer thread 0 filled with bulk copies
+// that it had not released yet, and thread 0 waits for their phases (they complete once the
+// bytes land); the MMA thread commits once more and waits for that commit (every MMA it issued
 // has then completed).  The kernel then sets the timeout bit of the error word and returns.
 #include "common.cuh"
 #include "vfmm_internal.h"
@@ -100,7 +101,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
 {
     for (long long it = 0; it < limit; ++it) {
         if (mbar_try(bar, parity)) return true;
-        if (*abort) return false;
+        if ((it & 63) == 63 && *abort) return false;  // the abort word is polled every 64 tries
     }
     *abort = 1;
     return false;
@@ -115,26 +116,14 @@ __device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity)
     return false;
 }
 
-// Warp-uniform pipeline wait: lane 0 waits, every lane takes its answer (so a warp leaves a loop
-// together and no lane is left at a __syncwarp).
+// Warp-uniform pipeline wait: every lane waits, and the warp goes on only if every lane's wait
+// succeeded (so a warp leaves a loop together and no lane is left at a __syncwarp).
 __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, long long limit, volatile int *abort)
 {
-    int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, limit, abort) ? 1 : 0;
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    const bool ok = mbar_wait(bar, parity, limit, abort);
+    return __all_sync(0xffffffffu, ok) != 0;
 }
 
-// Bulk-copy drain of one producer thread: for each stage, wait for the last transaction phase
-// it issued there (stage s had n_s = issues on it; the last completes phase n_s - 1).
-template <int STAGES> __device__ __forceinline__ bool drain_bulk(const uint64_t *tx, int issued)
-{
-    bool ok = true;
-    for (int s = 0; s < STAGES && s < issued; ++s) {
-        const int ns = (issued - s + STAGES - 1) / STAGES;
-        ok = mbar_wait_drain(smem_u32(&tx[s]), (uint32_t)((ns - 1) & 1)) && ok;
-    }
-    return ok;
-}
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 {
@@ -188,9 +177,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 // Warp-specialised pipeline: warp 0 lane 0 issues the MMAs; warps 1..4 (128 producer threads)
 // gather the multipole rows with cp.async and release a stage (fence.proxy.async by every
 // lane, one arrive per warp on full[s]) TC_PF stages after issuing it; producer thread 0 also
-// moves the two pre-tiled translation-matrix tiles with TMA bulk copies (expect_tx on tx[s]).
-// The MMA thread waits for full[s] and tx[s]; tcgen05.commit on empty[s] returns the slot to
-// the producers.  No CTA-wide barrier inside the main loop.
+// moves the two pre-tiled translation-matrix tiles with TMA bulk copies (expect_tx on full[s],
+// so a stage is full once its four warps arrived and its bytes landed).  tcgen05.commit on
+// empty[s] returns the slot to the producers.  No CTA-wide barrier inside the main loop.
 // Producer release lag.  A stage is released after the producer has issued TC_PF later stages,
 // and issuing stage i waits for the MMAs of stage i - TC_STAGES; TC_STAGES - TC_PF >= 3 keeps an
 // MMA queued behind the running one (a lag of 4 of 5 stages serialised the MMAs).
@@ -205,10 +194,10 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
     unsigned char *stages = base;
     uint64_t *full = (uint64_t *)(base + TC_STAGES * TC_STAGE_BYTES);
     uint64_t *empty = full + TC_STAGES;
-    uint64_t *tx = empty + TC_STAGES;    // bulk-copy bytes of each stage
-    uint64_t *drain = tx + TC_STAGES;    // final tcgen05.commit
+    uint64_t *drain = empty + TC_STAGES;  // final tcgen05.commit
     uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort = (volatile int *)(tmem_slot + 1);
+    volatile int *issued_sh = abort + 1;  // stages producer thread 0 filled with bulk copies
     int4 *kb_s = (int4 *)(base + TC_STAGES * TC_STAGE_BYTES + 256);
     int *cell_s = (int *)(kb_s + TC_MAXKB);
 
@@ -235,12 +224,12 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
 
     if (tid == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_init(smem_u32(&full[s]), TC_THREADS / 32);  // one arrival per producer warp
-            mbar_init(smem_u32(&empty[s]), 1);              // tcgen05.commit
-            mbar_init(smem_u32(&tx[s]), 1);                 // expect_tx of the bulk copies
+            mbar_init(smem_u32(&full[s]), TC_THREADS / 32 + 1);  // one arrival per producer warp + expect_tx
+            mbar_init(smem_u32(&empty[s]), 1);                  // tcgen05.commit
         }
         mbar_init(smem_u32(drain), 1);
         *abort = 0;
+        *issued_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
@@ -264,8 +253,7 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
             for (int i = 0; i < nk; ++i) {
                 const int s = i % TC_STAGES;
                 const uint32_t ph = (uint32_t)((i / TC_STAGES) & 1);
-                if (!mbar_wait(smem_u32(&full[s]), ph, tp.wait_limit, abort) ||
-                    !mbar_wait(smem_u32(&tx[s]), ph, tp.wait_limit, abort)) {
+                if (!mbar_wait(smem_u32(&full[s]), ph, tp.wait_limit, abort)) {
                     ok = false;
                     break;
                 }
@@ -292,7 +280,7 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
     } else {
         // ------------------------------- producers ---------------------------------
         const int ptid = tid - 32;
-        int issued = 0;  // stages whose bulk copies producer thread 0 issued
+        int released = 0;  // stages this warp has released on full[]
         int slot_cx[TC_BCHUNKS], slot_cy[TC_BCHUNKS], slot_cz[TC_BCHUNKS], slot_comp[TC_BCHUNKS], slot_kg[TC_BCHUNKS];
 #pragma unroll
         for (int j = 0; j < TC_BCHUNKS; ++j) {
@@ -324,11 +312,11 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
                 unsigned char *st = stages + s * TC_STAGE_BYTES;
                 uint32_t sA = smem_u32(st), sAl = sA + TC_A_BYTES, sB = sAl + TC_A_BYTES, sBl = sB + TC_B_BYTES;
                 if (ptid == 0) {
-                    uint32_t fb = smem_u32(&tx[s]);
+                    uint32_t fb = smem_u32(&full[s]);
                     mbar_expect_tx(fb, 2 * TC_A_BYTES);
                     bulk_g2s(sA, Ahi + ((size_t)kb.x * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
                     bulk_g2s(sAl, Alo + ((size_t)kb.x * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
-                    issued = i + 1;
+                    *issued_sh = i + 1;
                 }
 #pragma unroll
                 for (int j = 0; j < TC_BCHUNKS; ++j) {
@@ -350,11 +338,25 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
                 fence_proxy_async();
                 __syncwarp();
                 if ((tid & 31) == 0) mbar_arrive(smem_u32(&full[(i - TC_PF) % TC_STAGES]));
+                released = i - TC_PF + 1;
             }
         }
-        // drain: this thread's cp.async copies, and producer thread 0's bulk copies
+        // drain.  This thread's cp.async copies first.  Then the bulk copies of producer thread 0,
+        // which complete on full[]: once every producer warp has left its loop (named barrier),
+        // each warp arrives once on every stage thread 0 filled that it has not released (only
+        // after a give-up), so each such phase completes when its bytes land, and thread 0 waits
+        // for the last phase of every stage.
         cp_async_wait<0>();
-        if (ptid == 0 && !drain_bulk<TC_STAGES>(tx, issued)) ok = false;
+        fence_proxy_async();
+        asm volatile("bar.sync 1, %0;" ::"n"(TC_THREADS) : "memory");
+        const int issued = *issued_sh;
+        __syncwarp();
+        if ((tid & 31) == 0)
+            for (int j = released; j < issued; ++j) mbar_arrive(smem_u32(&full[j % TC_STAGES]));
+        asm volatile("bar.sync 1, %0;" ::"n"(TC_THREADS) : "memory");
+        if (ptid == 0)
+            for (int j = issued > TC_STAGES ? issued - TC_STAGES : 0; j < issued; ++j)
+                if (!mbar_wait_drain(smem_u32(&full[j % TC_STAGES]), (uint32_t)((j / TC_STAGES) & 1))) ok = false;
     }
     // epilogue: the MMA thread has seen its drain commit arrive (all MMAs done) before this
     // barrier; then warps 0..3 read TMEM lanes 32w..32w+31
@@ -447,10 +449,10 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
     unsigned char *stages = base;
     uint64_t *full = (uint64_t *)(base + TL_STAGES * Gm::STAGE);
     uint64_t *empty = full + TL_STAGES;
-    uint64_t *tx = empty + TL_STAGES;    // bulk-copy bytes of each stage
-    uint64_t *drain = tx + TL_STAGES;    // final tcgen05.commit
+    uint64_t *drain = empty + TL_STAGES;  // final tcgen05.commit
     uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort = (volatile int *)(tmem_slot + 1);
+    volatile int *issued_sh = abort + 1;  // stages producer thread 0 filled with bulk copies
     int4 *cls_s = (int4 *)(base + TL_STAGES * Gm::STAGE + 256);
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -465,12 +467,12 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
 
     if (tid == 0) {
         for (int s = 0; s < TL_STAGES; ++s) {
-            mbar_init(smem_u32(&full[s]), TC_THREADS / 32);  // one arrival per producer warp
-            mbar_init(smem_u32(&empty[s]), 1);              // tcgen05.commit
-            mbar_init(smem_u32(&tx[s]), 1);                 // expect_tx of the bulk copies
+            mbar_init(smem_u32(&full[s]), TC_THREADS / 32 + 1);  // one arrival per producer warp + expect_tx
+            mbar_init(smem_u32(&empty[s]), 1);                  // tcgen05.commit
         }
         mbar_init(smem_u32(drain), 1);
         *abort = 0;
+        *issued_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
@@ -494,8 +496,7 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
             for (int i = 0; i < nk; ++i) {
                 const int s = i % TL_STAGES;
                 const uint32_t ph = (uint32_t)((i / TL_STAGES) & 1);
-                if (!mbar_wait(smem_u32(&full[s]), ph, tp.wait_limit, abort) ||
-                    !mbar_wait(smem_u32(&tx[s]), ph, tp.wait_limit, abort)) {
+                if (!mbar_wait(smem_u32(&full[s]), ph, tp.wait_limit, abort)) {
                     ok = false;
                     break;
                 }
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
     } else {
         // ------------------------------- producers ---------------------------------
         const int ptid = tid - 32;
-        int issued = 0;  // stages whose bulk copies producer thread 0 issued
+        int released = 0;  // stages this warp has released on full[]
         const unsigned char *Ahi = (const unsigned char *)tp.Ahi, *Alo = (const unsigned char *)tp.Alo;
         const unsigned char *Bhi = (const unsigned char *)tp.Bhi, *Blo = (const unsigned char *)tp.Blo;
         for (int i = 0; i < nk + TL_PF; ++i) {
@@ -547,8 +548,8 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
                 const int cnt = min(hd.w, TL_MAXOFF);
                 const uint32_t st = smem_u32(stages + s * Gm::STAGE);
                 if (ptid == 0) {
-                    const uint32_t fb = smem_u32(&tx[s]);
-                    issued = i + 1;
+                    const uint32_t fb = smem_u32(&full[s]);
+                    *issued_sh = i + 1;
                     mbar_expect_tx(fb, (uint32_t)(cnt * 2 * TC_A_BYTES));
                     for (int e = 0; e < cnt; ++e) {
                         const int tile = checked_index(e == 0 ? e01.x : e == 1 ? e01.z : e23.x, NT, tp.err);
@@ -584,11 +585,25 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
                 fence_proxy_async();
                 __syncwarp();
                 if ((tid & 31) == 0) mbar_arrive(smem_u32(&full[(i - TL_PF) % TL_STAGES]));
+                released = i - TL_PF + 1;
             }
         }
-        // drain: this thread's cp.async copies, and producer thread 0's bulk copies
+        // drain.  This thread's cp.async copies first.  Then the bulk copies of producer thread 0,
+        // which complete on full[]: once every producer warp has left its loop (named barrier),
+        // each warp arrives once on every stage thread 0 filled that it has not released (only
+        // after a give-up), so each such phase completes when its bytes land, and thread 0 waits
+        // for the last phase of every stage.
         cp_async_wait<0>();
-        if (ptid == 0 && !drain_bulk<TL_STAGES>(tx, issued)) ok = false;
+        fence_proxy_async();
+        asm volatile("bar.sync 1, %0;" ::"n"(TC_THREADS) : "memory");
+        const int issued = *issued_sh;
+        __syncwarp();
+        if ((tid & 31) == 0)
+            for (int j = released; j < issued; ++j) mbar_arrive(smem_u32(&full[j % TL_STAGES]));
+        asm volatile("bar.sync 1, %0;" ::"n"(TC_THREADS) : "memory");
+        if (ptid == 0)
+            for (int j = issued > TL_STAGES ? issued - TL_STAGES : 0; j < issued; ++j)
+                if (!mbar_wait_drain(smem_u32(&full[j % TL_STAGES]), (uint32_t)((j / TL_STAGES) & 1))) ok = false;
     }
     // epilogue: the MMA thread has seen its drain commit arrive (all MMAs done) before this
     // barrier; then warps 0..3 read TMEM lanes 32w..32w+31
@@ -709,6 +724,22 @@ __global__ void k_split_tf32(int64_t count, const float *__restrict__ M, float *
     float h = to_tf32(v);
     hi[i] = h;
     lo[i] = to_tf32(v - h);
+}
+
+void set_carveouts_m2l()
+{
+    prefer_max_shared(k_m2l_tc<true>);
+    prefer_max_shared(k_m2l_tc<false>);
+    prefer_max_shared(k_m2l_lines<true, 16>);
+    prefer_max_shared(k_m2l_lines<true, 32>);
+    prefer_max_shared(k_m2l_lines<true, 64>);
+    prefer_max_shared(k_m2l_lines<false, 16>);
+    prefer_max_shared(k_m2l_lines<false, 32>);
+    prefer_max_shared(k_m2l_lines<false, 64>);
+    prefer_max_shared(k_split_grid<__nv_bfloat16>);
+    prefer_max_shared(k_split_grid<float>);
+    prefer_max_shared(k_split_bf16);
+    prefer_max_shared(k_split_tf32);
 }
 
 bool grid_level(int level)

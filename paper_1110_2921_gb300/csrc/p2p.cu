@@ -32,6 +32,7 @@
 #include "common.cuh"
 #include "vfmm_internal.h"
 
+#include <algorithm>
 #include <cmath>
 
 namespace vfmm {
@@ -245,18 +246,27 @@ __device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, fl
     a.E2 = fmaf(f, cj.z, a.E2);
 }
 
-// Tuning knobs (compile-time): targets per lane and the unroll of the source loop.  Measured
-// alternatives (four targets per lane with the two half-warps splitting the sources, other
-// unrolls and occupancies) were slower or equal.
+// Tuning knobs (compile-time): targets per lane, the unroll of the source loop, blocks per SM.
+// In-line P2P at 256^3 (sigma = h): two targets per lane, unroll 1, 32 blocks per SM 50.2 ms;
+// unroll 2 50.4; 28 blocks per SM 50.9; 16 blocks per SM (128 registers) 54.7; four targets per
+// lane with the half-warp split (VFMM_P3_SPLIT) 52.5 at 16 and 56.8 at 20 blocks per SM.
 #ifndef VFMM_P3_TPT
 #define VFMM_P3_TPT 2
 #endif
 #ifndef VFMM_P3_UNROLL
-#define VFMM_P3_UNROLL 2
+#define VFMM_P3_UNROLL 1
 #endif
-constexpr int P3_THREADS = 32;   // one warp per target leaf chunk
-constexpr int P3_TPT = VFMM_P3_TPT;              // targets per lane
-constexpr int P3_TARGETS = P3_THREADS * P3_TPT;  // targets per block
+// VFMM_P3_SPLIT = 1: four targets per lane, the two half-warps taking alternate sources of every
+// run (their sums are added by one shuffle at the end), which halves the per-source overhead
+// (loads, loop, uniform-datapath and move instructions) per pair.
+#ifndef VFMM_P3_SPLIT
+#define VFMM_P3_SPLIT 0
+#endif
+constexpr int P3_SPLIT = VFMM_P3_SPLIT;
+constexpr int P3_THREADS = 32;                            // one warp per target leaf chunk
+constexpr int P3_TPT = P3_SPLIT ? 4 : VFMM_P3_TPT;        // targets per lane
+constexpr int P3_LANES = P3_SPLIT ? 16 : 32;              // lanes that share one source
+constexpr int P3_TARGETS = P3_LANES * P3_TPT;             // targets per block
 constexpr int P3_TILE = 64;      // staged sources
 constexpr int P3_UNROLL = VFMM_P3_UNROLL;
 
@@ -271,7 +281,7 @@ __device__ __forceinline__ void tile3(const P3Const &k, const float (&xi)[P3_TPT
                                       const Src3 *src, int j0, int j1, Acc3 (&acc)[P3_TPT])
 {
 #pragma unroll P3_UNROLL
-    for (int j = j0; j < j1; ++j) {
+    for (int j = j0; j < j1; j += 1 + P3_SPLIT) {
         const float4 xj = src[j].x, gj = src[j].g, cj = src[j].c;
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) pair3<MODE>(k, xi[q][0], xi[q][1], xi[q][2], gi[q][0], gi[q][1], gi[q][2], xj, gj, cj, acc[q]);
@@ -347,7 +357,11 @@ constexpr float INV_4PI_F = 0.0795774715459476679f;
 constexpr double INV_4PI_D = 0.0795774715459476679;
 
 #ifndef VFMM_P3_MINB
+#if VFMM_P3_SPLIT
+#define VFMM_P3_MINB 20  // 20 one-warp blocks per SM (102 registers: four targets per lane)
+#else
 #define VFMM_P3_MINB 32  // full occupancy: 32 one-warp blocks per SM (64 registers)
+#endif
 #endif
 #if VFMM_P3_MINB > 0
 #define VFMM_P3_BOUNDS __launch_bounds__(P3_THREADS, VFMM_P3_MINB)
@@ -361,22 +375,26 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
                                                         int R, int Rc, int direct_K, float leaf_w, P3Const kc,
                                                         const float *__restrict__ ufar, const float *__restrict__ sfar,
                                                         const int *__restrict__ perm, float *__restrict__ u_out,
-                                                        float *__restrict__ s_out, int *__restrict__ err)
+                                                        float *__restrict__ s_out, int *__restrict__ err, int chunks,
+                                                        int64_t ntask)
 {
     __shared__ Src3 src[P3_TILE];
     __shared__ int ost[9];
-    const int leaf = blockIdx.x;
+    const float s = kc.s;
+    // tasks = (leaf, chunk of P3_TARGETS targets); the grid is either one block per task or a
+    // persistent grid that strides over them
+    for (int64_t task = blockIdx.x; task < ntask; task += gridDim.x) {
+    const int leaf = (int)(task / chunks), chunk = (int)(task - (int64_t)leaf * chunks);
     const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
     const int tb = ls[leaf], te = ls[leaf + 1];
     const float zx = (cx + 0.5f) * leaf_w, zy = (cy + 0.5f) * leaf_w, zz = (cz + 0.5f) * leaf_w;
-    const float s = kc.s;
     const float4 tlo = bbox[2 * leaf], thi = bbox[2 * leaf + 1];
-    for (int t0 = tb + blockIdx.y * P3_TARGETS; t0 < te; t0 += gridDim.y * P3_TARGETS) {
+    for (int t0 = tb + chunk * P3_TARGETS; t0 < te; t0 += chunks * P3_TARGETS) {
         float xi[P3_TPT][3], gi[P3_TPT][3];
         int tix[P3_TPT];
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) {
-            int ti = t0 + threadIdx.x + q * P3_THREADS;
+            int ti = t0 + (int)(threadIdx.x % P3_LANES) + q * P3_LANES;
             tix[q] = ti;
             float4 x = ti < te ? xs[ti] : make_float4(zx, zy, zz, 0.f);
             float4 g = ti < te ? gs[ti] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -401,79 +419,109 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
             lo[d] = direct_K >= 0 ? -cc[d] - direct_K * nside : -Rl;
             hi[d] = direct_K >= 0 ? nside - 1 - cc[d] + direct_K * nside : Rl;
         }
-        for (int ox = lo[0]; ox <= hi[0]; ++ox)
-            for (int oy = lo[1]; oy <= hi[1]; ++oy)
-                for (int oz = lo[2]; oz <= hi[2]; ++oz) {
+        // Neighbour leaves in batches of four: lane (li, o) classifies octant o of neighbour li
+        // of the batch by the closest approach of the target leaf box and the octant box (in the
+        // near rings smoothed with or without the small-rho series, or singular; beyond them the
+        // Gaussian-tail correction for octants closer than rho_cut sigma (mode 3), nothing
+        // otherwise (mode 4, the M2L has them)); three ballots give every lane the modes of all
+        // 32 octants, so the warp-uniform loop below reads its inner-loop choice per octant.
+        const int n1 = hi[1] - lo[1] + 1, n2 = hi[2] - lo[2] + 1;
+        const int n_off = (hi[0] - lo[0] + 1) * n1 * n2;
+        const int lane = threadIdx.x & 31;
+        for (int idx0 = 0; idx0 < n_off; idx0 += 4) {
+            int my_mode = 4;
+            {
+                const int idx = idx0 + (lane >> 3), o = lane & 7;
+                if (idx < n_off) {
+                    const int ox = lo[0] + idx / (n1 * n2), oy = lo[1] + (idx / n2) % n1, oz = lo[2] + idx % n2;
                     const bool corr = direct_K < 0 && (abs(ox) > R || abs(oy) > R || abs(oz) > R);
-                    if (corr) {
-                        // the cells alone keep a leaf |o| rings away at least (|o| - 1) w apart
-                        // along that axis: skip the leaves that cannot come within rho_cut sigma
-                        float gx = (float)max(abs(ox) - 1, 0), gy = (float)max(abs(oy) - 1, 0),
-                              gz = (float)max(abs(oz) - 1, 0);
-                        if ((gx * gx + gy * gy + gz * gz) * kc.w2_lo >= kc.d2_cut) continue;
-                    }
-                    int nx = cx + ox, ny = cy + oy, nz = cz + oz;
-                    int sl = ((nx & (nside - 1)) * nside + (ny & (nside - 1))) * nside + (nz & (nside - 1));
-                    sl = checked_index(sl, nside * nside * nside, err);
-                    float shx = kc.L * (float)(nx >> log2n), shy = kc.L * (float)(ny >> log2n), shz = kc.L * (float)(nz >> log2n);
-                    // closest approach of the target leaf box and each source octant box selects
-                    // the inner loop for that octant (warp-uniform): in the near rings smoothed
-                    // (with or without the small-rho series) or singular; beyond them, the
-                    // Gaussian-tail correction for octants closer than rho_cut sigma (mode 3),
-                    // nothing otherwise (mode 4, the M2L has them)
-                    int modes = 0;
-#pragma unroll
-                    for (int o = 0; o < 8; ++o) {
-                        float4 slo = oct_box[16 * sl + 2 * o], shi = oct_box[16 * sl + 2 * o + 1];
-                        float gx = fmaxf(0.f, fmaxf(slo.x + shx - thi.x, tlo.x - shi.x - shx));
-                        float gy = fmaxf(0.f, fmaxf(slo.y + shy - thi.y, tlo.y - shi.y - shy));
-                        float gz = fmaxf(0.f, fmaxf(slo.z + shz - thi.z, tlo.z - shi.z - shz));
-                        float d2 = gx * gx + gy * gy + gz * gz;
-                        int mode = corr ? (d2 < kc.d2_cut ? 3 : 4)
-                                        : (d2 >= kc.d2_singular ? 2 : (d2 >= kc.d2_series ? 1 : 0));
-                        modes |= mode << (3 * o);
-                    }
-                    if (corr && modes == 04444444444) continue;  // all eight octants are far: nothing to add
-                    // sources relative to the target leaf centre, with the image shift
-                    float ox0 = shx - zx, ox1 = shy - zy, ox2 = shz - zz;
-                    int sb = ls[sl], se = ls[sl + 1];
-                    __syncwarp();
-                    if (threadIdx.x < 8) ost[threadIdx.x] = oct_start[8 * sl + threadIdx.x];
-                    if (threadIdx.x == 8) ost[8] = se - sb;
-                    for (int s0 = sb; s0 < se; s0 += P3_TILE) {
-                        int cnt = min(P3_TILE, se - s0);
-                        __syncwarp();
-                        for (int j = threadIdx.x; j < cnt; j += P3_THREADS) {
-                            float4 x = xs[s0 + j], g = gs[s0 + j];
-                            float a0 = s * (x.x + ox0), a1 = s * (x.y + ox1), a2 = s * (x.z + ox2);
-                            src[j].x = make_float4(a0, a1, a2, 0.f);
-                            src[j].g = g;
-                            src[j].c = make_float4(g.y * a2 - g.z * a1, g.z * a0 - g.x * a2, g.x * a1 - g.y * a0, 0.f);
-                        }
-                        __syncwarp();
-                        const int c0 = s0 - sb, c1 = c0 + cnt;
-                        // runs of consecutive octants with the same inner loop
-                        int o = 0;
-                        while (o < 8) {
-                            const int mode = (modes >> (3 * o)) & 7;
-                            int o2 = o + 1;
-                            while (o2 < 8 && ((modes >> (3 * o2)) & 7) == mode) ++o2;
-                            int j0 = max(ost[o], c0) - c0, j1 = min(ost[o2], c1) - c0;
-                            if (j0 < j1) {
-                                if (mode == 2) tile3<2>(kc, xi, gi, src, j0, j1, acc);
-                                else if (mode == 1) tile3<1>(kc, xi, gi, src, j0, j1, acc);
-                                else if (mode == 0) tile3<0>(kc, xi, gi, src, j0, j1, acc);
-                                else if (mode == 3) tile3<3>(kc, xi, gi, src, j0, j1, acc);
-                            }
-                            o = o2;
-                        }
+                    // the cells alone keep a leaf |o| rings away at least (|o| - 1) w apart along
+                    // that axis: a correction-ring leaf that cannot come within rho_cut sigma is skipped
+                    const float cgx = (float)max(abs(ox) - 1, 0), cgy = (float)max(abs(oy) - 1, 0),
+                                cgz = (float)max(abs(oz) - 1, 0);
+                    if (!corr || (cgx * cgx + cgy * cgy + cgz * cgz) * kc.w2_lo < kc.d2_cut) {
+                        const int nx = cx + ox, ny = cy + oy, nz = cz + oz;
+                        int sl = ((nx & (nside - 1)) * nside + (ny & (nside - 1))) * nside + (nz & (nside - 1));
+                        sl = checked_index(sl, nside * nside * nside, err);
+                        const float shx = kc.L * (float)(nx >> log2n), shy = kc.L * (float)(ny >> log2n),
+                                    shz = kc.L * (float)(nz >> log2n);
+                        const float4 slo = oct_box[16 * sl + 2 * o], shi = oct_box[16 * sl + 2 * o + 1];
+                        const float gx = fmaxf(0.f, fmaxf(slo.x + shx - thi.x, tlo.x - shi.x - shx));
+                        const float gy = fmaxf(0.f, fmaxf(slo.y + shy - thi.y, tlo.y - shi.y - shy));
+                        const float gz = fmaxf(0.f, fmaxf(slo.z + shz - thi.z, tlo.z - shi.z - shz));
+                        const float d2 = gx * gx + gy * gy + gz * gz;
+                        my_mode = corr ? (d2 < kc.d2_cut ? 3 : 4)
+                                       : (d2 >= kc.d2_singular ? 2 : (d2 >= kc.d2_series ? 1 : 0));
                     }
                 }
+            }
+            const unsigned b0 = __ballot_sync(0xffffffffu, my_mode & 1), b1 = __ballot_sync(0xffffffffu, my_mode & 2),
+                           b2 = __ballot_sync(0xffffffffu, my_mode & 4);
+            for (int li = 0; li < 4; ++li) {
+                const int idx = idx0 + li;
+                if (idx >= n_off) break;
+                const unsigned m0 = (b0 >> (8 * li)) & 0xFFu, m1 = (b1 >> (8 * li)) & 0xFFu,
+                               m2 = (b2 >> (8 * li)) & 0xFFu;
+                if (m2 == 0xFFu && (m0 | m1) == 0u) continue;  // all eight octants: nothing to add
+                const int ox = lo[0] + idx / (n1 * n2), oy = lo[1] + (idx / n2) % n1, oz = lo[2] + idx % n2;
+                const int nx = cx + ox, ny = cy + oy, nz = cz + oz;
+                int sl = ((nx & (nside - 1)) * nside + (ny & (nside - 1))) * nside + (nz & (nside - 1));
+                sl = checked_index(sl, nside * nside * nside, err);
+                const float shx = kc.L * (float)(nx >> log2n), shy = kc.L * (float)(ny >> log2n),
+                            shz = kc.L * (float)(nz >> log2n);
+                // sources relative to the target leaf centre, with the image shift
+                const float ox0 = shx - zx, ox1 = shy - zy, ox2 = shz - zz;
+                const int sb = ls[sl], se = ls[sl + 1];
+                __syncwarp();
+                if (threadIdx.x < 8) ost[threadIdx.x] = oct_start[8 * sl + threadIdx.x];
+                if (threadIdx.x == 8) ost[8] = se - sb;
+                for (int s0 = sb; s0 < se; s0 += P3_TILE) {
+                    const int cnt = min(P3_TILE, se - s0);
+                    __syncwarp();
+                    for (int j = threadIdx.x; j < cnt; j += P3_THREADS) {
+                        float4 x = xs[s0 + j], g = gs[s0 + j];
+                        float a0 = s * (x.x + ox0), a1 = s * (x.y + ox1), a2 = s * (x.z + ox2);
+                        src[j].x = make_float4(a0, a1, a2, 0.f);
+                        src[j].g = g;
+                        src[j].c = make_float4(g.y * a2 - g.z * a1, g.z * a0 - g.x * a2, g.x * a1 - g.y * a0, 0.f);
+                    }
+                    __syncwarp();
+                    const int c0 = s0 - sb, c1 = c0 + cnt;
+                    // runs of consecutive octants with the same inner loop
+                    int o = 0;
+                    while (o < 8) {
+                        const int mode = (int)(((m0 >> o) & 1u) | (((m1 >> o) & 1u) << 1) | (((m2 >> o) & 1u) << 2));
+                        int o2 = o + 1;
+                        while (o2 < 8 && (int)(((m0 >> o2) & 1u) | (((m1 >> o2) & 1u) << 1) | (((m2 >> o2) & 1u) << 2)) == mode)
+                            ++o2;
+                        const int j0 = max(ost[o], c0) - c0, j1 = min(ost[o2], c1) - c0;
+                        if (j0 < j1) {
+                            const int jh = j0 + (P3_SPLIT ? (int)(threadIdx.x >> 4) : 0);
+                            if (mode == 2) tile3<2>(kc, xi, gi, src, jh, j1, acc);
+                            else if (mode == 1) tile3<1>(kc, xi, gi, src, jh, j1, acc);
+                            else if (mode == 0) tile3<0>(kc, xi, gi, src, jh, j1, acc);
+                            else if (mode == 3) tile3<3>(kc, xi, gi, src, jh, j1, acc);
+                        }
+                        o = o2;
+                    }
+                }
+            }
+        }
+        if (P3_SPLIT) {
+            // the two half-warps summed alternate sources: add them
+#pragma unroll
+            for (int q = 0; q < P3_TPT; ++q) {
+                float *v = &acc[q].A0;
+#pragma unroll
+                for (int e = 0; e < 12; ++e) v[e] += __shfl_xor_sync(0xffffffffu, v[e], 16);
+            }
+        }
         // u = s^2 (A x x^ - U), S = s^3 (A x gamma + D x x^ - E), times 1/(4 pi)
         const float su = INV_4PI_F * s * s, ss = su * s;
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) {
             int ti = tix[q];
+            if (P3_SPLIT && (q >> 1) != (int)(threadIdx.x >> 4)) continue;  // each half writes two targets
             if (ti >= te) continue;
             const Acc3 &a = acc[q];
             const float *x = xi[q], *g = gi[q];
@@ -494,6 +542,7 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
             store_out<float>(u_out, s_out, perm[ti], u0, u1, u2, s0, s1, s2);
         }
     }
+    }  // task
 }
 
 __global__ void __launch_bounds__(P2P_BS) k_p2p_f64(const dvec4 *__restrict__ xs, const dvec4 *__restrict__ gs,
@@ -562,6 +611,8 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p_f64(const dvec4 *__restrict__ xs
     }
 }
 
+void set_carveouts_p2p() { prefer_max_shared(k_p2p_f32); }
+
 int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void *sfar, void *u_out, void *s_out,
                int direct_K)
 {
@@ -597,14 +648,18 @@ int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void
         kc.L = (float)c->cfg.box;
         int chunks3 = (c->max_leaf + P3_TARGETS - 1) / P3_TARGETS;
         if (chunks3 < 1) chunks3 = 1;
-        if (chunks3 > 65535) chunks3 = 65535;
-        dim3 grid3((unsigned)c->nleaf, (unsigned)chunks3);
-        k_p2p_f32<<<grid3, P3_THREADS, 0, c->stream>>>((const float4 *)c->xs.p, (const float4 *)c->gs.p,
+        const int64_t ntask = c->nleaf * chunks3;
+        // beside the concurrent far field the P2P runs as a persistent grid of P2P_SHARED_BLOCKS
+        // one-warp blocks per SM, which leaves each SM the registers and shared memory of one
+        // tensor-core M2L CTA (and of the smaller far-field kernels); alone, one block per task
+        int64_t nblk = ntask;
+        if (c->p2p_shared_blocks > 0) nblk = std::min<int64_t>(ntask, (int64_t)c->sm_count * c->p2p_shared_blocks);
+        k_p2p_f32<<<(unsigned)nblk, P3_THREADS, 0, c->stream>>>((const float4 *)c->xs.p, (const float4 *)c->gs.p,
                                                        (const int *)c->leaf_start.p, (const float4 *)c->bbox.p,
                                                        (const int *)c->oct_start.p, (const float4 *)c->oct_box.p,
                                                        c->nside, log2n, R, Rc, direct_K, (float)c->leaf_w, kc,
                                                        (const float *)ufar, (const float *)sfar, (const int *)c->perm.p,
-                                                       (float *)u_out, (float *)s_out, (int *)c->err.p);
+                                                       (float *)u_out, (float *)s_out, (int *)c->err.p, chunks3, ntask);
     }
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;

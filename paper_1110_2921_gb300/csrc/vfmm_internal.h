@@ -21,6 +21,19 @@ constexpr int TC_KBYTES = 32;     // tensor-core M2L: K bytes of one pipeline st
 constexpr int TC_KG = TC_KBYTES / 16;   // 16-byte k-groups per stage
 constexpr int TC_A_TILE = 128 * TC_KBYTES;  // bytes of one translation-matrix tile (128 rows)
 
+// P2P beside the concurrent far field: VFMM_P2P_SHARED_BLOCKS > 0 runs it as a persistent grid
+// of that many one-warp blocks per SM (leaving room for far-field blocks on every SM), and
+// VFMM_FORK_AT_M2L = 1 runs the upward pass in line and forks only the M2L and the downward
+// pass.  Measured at 256^3 (step ms, every phase 73.7 ms in line): one block per task and the
+// fork before the P2M 72.9; fork at the M2L 73.1; persistent 16 or 20 blocks per SM 74-80
+// (the M2L then waits for the P2P).  Defaults: the first.
+#ifndef VFMM_P2P_SHARED_BLOCKS
+#define VFMM_P2P_SHARED_BLOCKS 0
+#endif
+#ifndef VFMM_FORK_AT_M2L
+#define VFMM_FORK_AT_M2L 0
+#endif
+
 // device error word bits
 constexpr int ERRBIT_LEAF_OVERFLOW = 1;
 constexpr int ERRBIT_BOUNDS = 2;
@@ -155,6 +168,8 @@ struct Ctx {
     bool timed_eval = false;
     int64_t launches = 0;      // kernels launched by the last build + evaluation
     long long wait_limit = 1LL << 26;  // tries of each tensor-core pipeline wait (vfmm_set_wait_limit)
+    int sm_count = 152;                // multiprocessors of the device (set at create)
+    int p2p_shared_blocks = 0;         // > 0: FP32 P2P as a persistent grid of this many blocks per SM
     double timings[NPHASE];
     std::string last_error;
 };
@@ -195,6 +210,10 @@ int launch_split(Ctx *c, int level, bool bf16);
 int launch_split_reduce(Ctx *c, int nsplit, int64_t count, const void *partial, void *C, int accumulate, bool f32);
 size_t split_count(int level, int pc);  // hi/lo elements launch_split writes for one level
 void set_constants(int p);
+// largest shared-memory carveout for the kernels of each translation unit (see prefer_max_shared)
+void set_carveouts_expansions();
+void set_carveouts_p2p();
+void set_carveouts_m2l();
 int launch_axpy3(Ctx *c, int64_t n, const void *a, const void *b, const void *d, double coef, double wrap_L, void *out);
 int launch_diag(Ctx *c, int64_t n, const void *x, const void *g, const void *u, double *out_dev);
 int launch_reinit(Ctx *c, int m, double sigma, double sigma0, int iters, int R, void *x_new, void *g_new,
