@@ -1152,10 +1152,11 @@ int launch_root_t(Ctx *c)
 
 namespace vfmm {
 
+// the far-field kernels (which may share SMs with the P2P); the gather of the strengths and the
+// final add of the far field run alone and keep the default split (the add of the far field
+// is 2.4x slower with the largest shared carveout, i.e. the smallest L1)
 void set_carveouts_expansions()
 {
-    prefer_max_shared(k_gather_gamma<float>);
-    prefer_max_shared(k_gather_gamma<double>);
     prefer_max_shared(k_p2m<float>);
     prefer_max_shared(k_p2m<double>);
     prefer_max_shared(k_gemm<float>);
@@ -1168,7 +1169,6 @@ void set_carveouts_expansions()
     prefer_max_shared(k_root_lattice<double>);
     prefer_max_shared(k_l2p<float, VFMM_L2P_PP>);
     prefer_max_shared(k_l2p<double, 1>);
-    prefer_max_shared(k_add_far);
 }
 
 }  // namespace vfmm

@@ -1,8 +1,8 @@
 """Parity at the benchmark sizes, in the launch configuration bench.py times.
 
-* 256^3 (16,777,216 particles, p = 10, sigma = h, BF16x3 M2L): sampled targets against the FP64
-  direct sum over the central 27 boxes (FMM with no super-level images: the same tree, lists
-  and kernels as the benchmark, whose 27^3 images differ only by the root lattice operator).
+* 256^3 (16,777,216 particles, p = 10, sigma = h, BF16x3 M2L, 27^3 images): the benchmark's
+  handle against the FP64 oracle's full 27^3-box sum at 16 stored targets, and the same tree with
+  the central 27 boxes at 160 stored targets (faces and interior).
 * 128^3, all particles: the fully periodic field (Fourier series of the smoothed vorticity)
   against the FMM with 6 super-levels of images (2187^3 boxes), u compared after removing the
   uniform velocity that the cube-truncated image sum carries.
@@ -18,16 +18,50 @@ from gpu_util import rel_l2, rel_l2_demeaned, run_fmm
 pytestmark = pytest.mark.gpu
 
 
-def test_bench_workload_256cubed_sampled():
+def _golden256():
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_field256
+    return make_field256.load()
+
+
+def _per_target(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+def test_bench_workload_256cubed_timed_config():
+    # The benchmark's workload and handle (256^3, p = 10, sigma = h, BF16x3 M2L, 27^3 images):
+    # the full 27^3-box definition at 16 targets (8 random, 8 within h of a face), oracle values
+    # stored by tests/golden/make_field256.py (central 27 boxes + the far-image increment); and the
+    # same tree with the 27 central boxes (S = 0) at 160 targets (128 random, 32 within h of a
+    # face), which separates the near/far parts (exact by linearity) and compares the faces with
+    # the interior (Section 5.7: the periodic FMM is accurate at the edges of the domain)
+    gd = _golden256()
     f = wl.make_vortex_lattice(256, 4, 1)
-    tid = wl.target_subset(256 ** 3, 12, seed=3)
-    uo, so = oracle.direct(f["x"], f["alpha"], f["sigma"], K=1, targets=tid)
-    u, s, info = run_fmm(f["x"], f["alpha"], f["sigma"], p=10, periodic_levels=0, m2l="bf16x3")
-    # one near ring; the second ring goes to the M2L with the Gaussian-tail correction
+    tid, face = gd["index"], gd["face"]
+    full = ~np.isnan(gd["u_far"][:, 0])
+    u2, s2, info = run_fmm(f["x"], f["alpha"], f["sigma"], p=10, periodic_levels=2, m2l="bf16x3")
     assert info["depth"] == 6 and info["near_rings"] == 1 and info["correction_rings"] == 2
-    eu, es = rel_l2(u[tid], uo), rel_l2(s[tid], so)
-    print("256^3 sampled: u %.3e S %.3e" % (eu, es))
+    uo = gd["u_near"][full] + gd["u_far"][full]
+    so = gd["S_near"][full] + gd["S_far"][full]
+    eu, es = rel_l2(u2[tid[full]], uo), rel_l2(s2[tid[full]], so)
+    pu, ps = _per_target(u2[tid[full]], uo), _per_target(s2[tid[full]], so)
+    print("256^3, S = 2, 16 targets: rel-L2 u %.3e S %.3e; per target max u %.3e S %.3e" % (eu, es, pu.max(), ps.max()))
     assert eu < 1e-4 and es < 1e-3
+    u0, s0, _ = run_fmm(f["x"], f["alpha"], f["sigma"], p=10, periodic_levels=0, m2l="bf16x3")
+    eu0, es0 = rel_l2(u0[tid], gd["u_near"]), rel_l2(s0[tid], gd["S_near"])
+    pu0, ps0 = _per_target(u0[tid], gd["u_near"]), _per_target(s0[tid], gd["S_near"])
+    fu, iu = rel_l2(u0[tid[face]], gd["u_near"][face]), rel_l2(u0[tid[~face]], gd["u_near"][~face])
+    fs, is_ = rel_l2(s0[tid[face]], gd["S_near"][face]), rel_l2(s0[tid[~face]], gd["S_near"][~face])
+    print("256^3, S = 0, 160 targets: rel-L2 u %.3e S %.3e; per target max u %.3e S %.3e; "
+          "faces u %.3e S %.3e, interior u %.3e S %.3e" % (eu0, es0, pu0.max(), ps0.max(), fu, fs, iu, is_))
+    assert eu0 < 1e-4 and es0 < 1e-3
+    assert fu < 1e-4 and fs < 1e-3
+    # the image increment of the GPU (S = 2 minus S = 0) against the oracle's far increment
+    ei = rel_l2((u2 - u0)[tid[full]], gd["u_far"][full])
+    print("image increment: rel-L2 %.3e" % ei)
+    assert ei < 1e-3
 
 
 def test_fully_periodic_128cubed_all_particles():
