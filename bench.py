@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--check", type=int, default=16, help="sampled targets for the oracle error (0 = off)")
     ap.add_argument("--cpu-targets", type=int, default=0, help="oracle targets for cpu_baseline (0 = one per host core)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--concurrent-far", type=int, default=-1,
+                    help="1: far field on a side stream beside the P2P; 0: every phase in line; -1: library default")
     ap.add_argument("--peaks", type=int, default=1, help="measure the FP32/MUFU/FP64/TF32/BF16 peaks (probe kernels)")
     ap.add_argument("--workload", default="eval", choices=["eval", "timestep"],
                     help="eval: u + S per step (the metric); timestep: ten Heun steps + one reinitialisation")
@@ -424,8 +426,9 @@ def main():
     G = torch.tensor(f["alpha"], dtype=torch.float32, device=dev)
     U = torch.empty_like(G)
     S = torch.empty_like(G)
+    cf = {} if args.concurrent_far < 0 else {"concurrent_far": args.concurrent_far}
     h = vf.VortexFMM(p=args.p, periodic_levels=args.periodic_levels, m2l=args.m2l, rho_cut=args.rho_cut,
-                     depth=args.depth)
+                     depth=args.depth, **cf)
     stream = torch.cuda.current_stream()
 
     ev_pairs = []
