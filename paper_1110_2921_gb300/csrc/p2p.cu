@@ -247,9 +247,12 @@ __device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, fl
 }
 
 // Tuning knobs (compile-time): targets per lane, the unroll of the source loop, blocks per SM.
-// In-line P2P at 256^3 (sigma = h): two targets per lane, unroll 1, 32 blocks per SM 50.2 ms;
-// unroll 2 50.4; 28 blocks per SM 50.9; 16 blocks per SM (128 registers) 54.7; four targets per
-// lane with the half-warp split (VFMM_P3_SPLIT) 52.5 at 16 and 56.8 at 20 blocks per SM.
+// In-line P2P at 256^3 (sigma = h), before the full-tile loop: two targets per lane, unroll 1,
+// 32 blocks per SM 50.2 ms; unroll 2 50.4; 28 blocks per SM 50.9; 16 blocks per SM (128
+// registers) 54.7; four targets per lane with the half-warp split (VFMM_P3_SPLIT) 52.5 at 16
+// and 56.8 at 20 blocks per SM.  After the warp-parallel octant classification (44.5 ms at
+// 32 blocks per SM), the full-tile loop unrolled 2 / 4 / 8 / 16 / 32: 44.7 / 44.4 / 43.6 /
+// 45.8 / 58.4 ms; unroll 8 at 28 / 24 blocks per SM: 43.4 / 44.2 ms.
 #ifndef VFMM_P3_TPT
 #define VFMM_P3_TPT 2
 #endif
@@ -282,6 +285,25 @@ __device__ __forceinline__ void tile3(const P3Const &k, const float (&xi)[P3_TPT
 {
 #pragma unroll P3_UNROLL
     for (int j = j0; j < j1; j += 1 + P3_SPLIT) {
+        const float4 xj = src[j].x, gj = src[j].g, cj = src[j].c;
+#pragma unroll
+        for (int q = 0; q < P3_TPT; ++q) pair3<MODE>(k, xi[q][0], xi[q][1], xi[q][2], gi[q][0], gi[q][1], gi[q][2], xj, gj, cj, acc[q]);
+    }
+}
+
+// A whole staged tile with one inner loop (the common case: every octant of a near-ring leaf
+// takes the same kernel): a compile-time trip count lets the loads use immediate offsets and
+// drops most of the per-source loop control.
+#ifndef VFMM_P3_FULLTILE
+#define VFMM_P3_FULLTILE 8  // unroll of the full-tile loop; 0 = the general loop only
+#endif
+constexpr int P3_FULL_UNROLL = VFMM_P3_FULLTILE > 0 ? VFMM_P3_FULLTILE : 1;
+template <int MODE>
+__device__ __forceinline__ void tile3_full(const P3Const &k, const float (&xi)[P3_TPT][3], const float (&gi)[P3_TPT][3],
+                                           const Src3 *src, Acc3 (&acc)[P3_TPT])
+{
+#pragma unroll P3_FULL_UNROLL
+    for (int j = 0; j < P3_TILE; ++j) {
         const float4 xj = src[j].x, gj = src[j].g, cj = src[j].c;
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) pair3<MODE>(k, xi[q][0], xi[q][1], xi[q][2], gi[q][0], gi[q][1], gi[q][2], xj, gj, cj, acc[q]);
@@ -360,7 +382,7 @@ constexpr double INV_4PI_D = 0.0795774715459476679;
 #if VFMM_P3_SPLIT
 #define VFMM_P3_MINB 20  // 20 one-warp blocks per SM (102 registers: four targets per lane)
 #else
-#define VFMM_P3_MINB 32  // full occupancy: 32 one-warp blocks per SM (64 registers)
+#define VFMM_P3_MINB 28  // 28 one-warp blocks per SM (73 registers)
 #endif
 #endif
 #if VFMM_P3_MINB > 0
@@ -495,7 +517,10 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
                         while (o2 < 8 && (int)(((m0 >> o2) & 1u) | (((m1 >> o2) & 1u) << 1) | (((m2 >> o2) & 1u) << 2)) == mode)
                             ++o2;
                         const int j0 = max(ost[o], c0) - c0, j1 = min(ost[o2], c1) - c0;
-                        if (j0 < j1) {
+                        if (VFMM_P3_FULLTILE > 0 && !P3_SPLIT && j0 == 0 && j1 == P3_TILE && (mode == 1 || mode == 3)) {
+                            if (mode == 1) tile3_full<1>(kc, xi, gi, src, acc);
+                            else tile3_full<3>(kc, xi, gi, src, acc);
+                        } else if (j0 < j1) {
                             const int jh = j0 + (P3_SPLIT ? (int)(threadIdx.x >> 4) : 0);
                             if (mode == 2) tile3<2>(kc, xi, gi, src, jh, j1, acc);
                             else if (mode == 1) tile3<1>(kc, xi, gi, src, jh, j1, acc);
