@@ -81,8 +81,9 @@ def test_fully_periodic_128cubed_all_particles():
 
 @pytest.fixture(scope="module")
 def case64():
+    # config 2: a random 4096-particle target subset of the 64^3 field (k0 = 8)
     f = wl.make_vortex_lattice(64, 8, 1)
-    tid = wl.target_subset(64 ** 3, 64, seed=3)
+    tid = wl.target_subset(64 ** 3, 4096, seed=3)
     uo, so = oracle.direct(f["x"], f["alpha"], f["sigma"], K=1, targets=tid)
     return f, tid, uo, so
 
