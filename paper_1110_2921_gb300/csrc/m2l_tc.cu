@@ -35,9 +35,11 @@
 #include "common.cuh"
 #include "vfmm_internal.h"
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 namespace vfmm {
 
@@ -397,51 +399,74 @@ __global__ void __launch_bounds__(TC_WS_THREADS, 2) k_m2l_tc(TcParams tp)
 // Source-line variant for levels with 16 to 64 cells per side and parity.
 //
 // The hi/lo multipoles of the level are first rearranged by K slice and parity into
-//   G[slice][b][X][Y][Zp][component][32 bytes of coefficients],  b = parity (bx, by, bz),
-//   Zp = Z + 2 (two halo cells on each side of every z-line, copied periodically),
-// so that one K slice of a source line is one contiguous run of rows.  The CTA walks the K
-// slices in the outer loop: the CTAs resident at one time then share the slice's source lines
-// in L2.
-// A CTA owns whole z-lines of target cells of one parity g (128 cells: N = 384 columns of TMEM).
-// For an offset t the sources of a target line are one z-line of G (parity b = (g + t) mod 2,
-// line shifted by (g + t) >> 1 in x and y) read through a z window shifted by shz = (g_z + t_z) >> 1.
-// Offsets that share (b, shx, shy) form a class (up to three offsets, differing in shz): the
-// class's source lines are gathered into shared memory once per K slice, in the no-swizzle
-// K-major layout with 16-byte rows ([k-group][row][16 B]) and rows ordered (Zp, line,
-// component), so the window of every offset of the class is one contiguous run of 384 rows
-// starting 3 LINES (shz + 2) rows in: two MMAs (N = 192) per offset and split product.  Each
-// gathered source row serves all offsets of its class and each translation-matrix tile 384
-// columns.
+//   G[slice][b][X][kg][Zp][Yp][component][16 bytes],  b = parity (bx, by, bz), kg = k-group,
+//   Zp = Z + 2 and Yp = Y + 2 (two halo cells on each side, copied periodically),
+// so that the rows a CTA needs from one source x-column form one box of a 5-d tensor that a
+// single TMA tensor copy lands in shared memory in the MMA's operand layout.  The CTA walks the
+// K slices in the outer loop: the CTAs resident at one time then share the slice's source lines
+// in L2.  The grid's fastest index is the target parity, so the eight parities of one group of
+// lines (which read the same source lines) run together.
+// A CTA owns whole z-lines of target cells of one parity g (128 cells: N = 384 columns of TMEM):
+// LINES consecutive y-lines of one x-column.  For an offset t the sources of a target line are
+// one z-line of G (parity b = (g + t) mod 2, shifted by (g + t) >> 1 in x and y) read through a
+// z window shifted by shz = (g_z + t_z) >> 1.  Offsets that share (b, shx, shy) form a class (up
+// to three offsets, differing in shz): the class's source lines are copied into shared memory
+// once per K slice, in the no-swizzle K-major layout with 16-byte rows ([k-group][row][16 B])
+// and rows ordered (Zp, line, component), so the window of every offset of the class is one
+// contiguous run of 384 rows starting 3 LINES (shz + 2) rows in: two MMAs (N = 192) per offset
+// and split product.  Each source row copied serves all offsets of its class and each
+// translation-matrix tile 384 columns.
+//
+// One thread of warp 1 moves everything with TMA (the translation tiles as bulk copies, the
+// source lines as one tensor copy per hi/lo), all completing on the stage's transaction
+// barrier; one thread of warp 0 issues the MMAs; all four warps read TMEM in the epilogue.
 constexpr int TL_CELLS = 128;              // target cells per CTA (whole z-lines)
 constexpr int TL_N = 3 * TL_CELLS;         // accumulator columns
-constexpr int TL_HALO = 2;                 // |shz| <= 2
+constexpr int TL_HALO = 2;                 // |shx|, |shy|, |shz| <= 2 (two near rings)
 constexpr int TL_MAXOFF = 3;               // offsets per class (the z parity leaves at most three)
 #ifndef VFMM_TL_STAGES
 #define VFMM_TL_STAGES 3
 #endif
 constexpr int TL_STAGES = VFMM_TL_STAGES;
-constexpr int TL_PF = TL_STAGES >= 4 ? 2 : 1;
 constexpr int TL_MAXCLS = 96;
 constexpr int TL_TMEM_COLS = 512;
-constexpr int TL_THREADS = 32 + TC_THREADS;  // MMA warp + 4 producer warps
-// shared bytes of one stage: up to four A tiles (hi, lo) and the class's source lines (hi, lo)
+constexpr int TL_THREADS = 128;            // warp 0: MMA issuer, warp 1: TMA producer; all: epilogue
+// shared bytes of one stage: up to three A tile pairs (hi, lo) and the class's source lines (hi, lo)
 template <int H> struct TlGeom {
     static constexpr int LINES = TL_CELLS / H;
-    static constexpr int ROWS_LINE = (H + 2 * TL_HALO) * 3;  // rows of one source line in G
-    static constexpr int ROWS = (H + 2 * TL_HALO) * LINES * 3;  // staged rows (Zp, line, component)
+    static constexpr int YP = H + 2 * TL_HALO;               // y extent of G (with halo)
+    static constexpr int ZP = H + 2 * TL_HALO;               // z extent of G (with halo)
+    static constexpr int ROWS = ZP * LINES * 3;              // staged rows (Zp, line, component)
     static constexpr int ROW_Z = LINES * 3;                  // staged rows per z step
     static constexpr int PLANE = ROWS * 16;                  // bytes of one 16-byte k-group plane
     static constexpr int A_BYTES = TL_MAXOFF * 2 * TC_A_BYTES;
-    static constexpr int B_BYTES = 2 * TC_KG * PLANE;        // hi and lo
+    static constexpr int BOX_BYTES = TC_KG * PLANE;          // one tensor copy (hi or lo)
+    static constexpr int B_BYTES = 2 * BOX_BYTES;            // hi and lo
     static constexpr int STAGE = (A_BYTES + B_BYTES + 1023) / 1024 * 1024;
     static constexpr int SMEM = TL_STAGES * STAGE + 1024 + 256 + TL_MAXCLS * 48;
-    static constexpr int CHUNKS = ROWS * TC_KG;              // 16-byte copies per stage (each of hi, lo)
+    static constexpr int BOX_X = ROW_Z * 8;                  // innermost box extent in 2-byte elements
     static_assert(TL_N == 2 * 192, "two MMAs of N = 192 per offset and product");
+    static_assert(TC_KG == 2, "the tensor box holds two 16-byte k-groups");
+    static_assert(BOX_X <= 256 && ZP <= 256, "TMA box extents");
+    static_assert((A_BYTES % 128) == 0 && (PLANE % 128) == 0, "128-byte aligned TMA destinations");
     static_assert(SMEM <= 232448, "shared memory per CTA");
 };
 
+// TMA tensor copy of a 5-d box global -> shared, completing on `bar` (transaction bytes)
+__device__ __forceinline__ void tensor_g2s_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                              int c4, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
 template <bool BF16, int H>
-__global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const int4 *__restrict__ cls)
+__global__ void __launch_bounds__(TL_THREADS, 1)
+    k_m2l_lines(TcParams tp, const int4 *__restrict__ cls, const __grid_constant__ CUtensorMap tm_hi,
+                const __grid_constant__ CUtensorMap tm_lo)
 {
     using Gm = TlGeom<H>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -452,13 +477,12 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
     uint64_t *drain = empty + TL_STAGES;  // final tcgen05.commit
     uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort = (volatile int *)(tmem_slot + 1);
-    volatile int *issued_sh = abort + 1;  // stages producer thread 0 filled with bulk copies
     int4 *cls_s = (int4 *)(base + TL_STAGES * Gm::STAGE + 256);
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int g = blockIdx.y;
+    const int g = blockIdx.x;                  // target parity (the fastest grid index)
     const int n = tp.n;
-    const int line0 = blockIdx.x * Gm::LINES;  // first target line (px * H + py) of this CTA
+    const int line0 = blockIdx.y * Gm::LINES;  // first target line (px * H + py) of this CTA
     const int ncls = min(tp.kb_cnt[g], TL_MAXCLS);
     for (int q = tid; q < 3 * ncls; q += TL_THREADS) cls_s[q] = cls[3 * tp.kb_off[g] + q];
     const int nchunk = tp.nchunk;
@@ -467,12 +491,11 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
 
     if (tid == 0) {
         for (int s = 0; s < TL_STAGES; ++s) {
-            mbar_init(smem_u32(&full[s]), TC_THREADS / 32 + 1);  // one arrival per producer warp + expect_tx
-            mbar_init(smem_u32(&empty[s]), 1);                  // tcgen05.commit
+            mbar_init(smem_u32(&full[s]), 1);   // the producer's expect_tx arrival; completes when the bytes land
+            mbar_init(smem_u32(&empty[s]), 1);  // tcgen05.commit
         }
         mbar_init(smem_u32(drain), 1);
         *abort = 0;
-        *issued_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
@@ -487,129 +510,91 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
 
-    if (warp == 0) {
+    if (tid == 0) {
         // ------------------------------- MMA issuer -------------------------------
-        if (tid == 0) {
-            const uint32_t fmt = BF16 ? 1u : 2u;
-            const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(192 >> 3) << 17) |
-                                   ((uint32_t)(TC_M >> 4) << 24);
-            for (int i = 0; i < nk; ++i) {
-                const int s = i % TL_STAGES;
-                const uint32_t ph = (uint32_t)((i / TL_STAGES) & 1);
-                if (!mbar_wait(smem_u32(&full[s]), ph, tp.wait_limit, abort)) {
-                    ok = false;
-                    break;
-                }
-                fence_proxy_async();  // producer cp.async writes (generic proxy) before the MMA reads
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                const int ci = i % ncls;
-                const int4 hd = cls_s[3 * ci], e01 = cls_s[3 * ci + 1], e23 = cls_s[3 * ci + 2];
-                const int cnt = min(hd.w, TL_MAXOFF);
-                const uint32_t st = smem_u32(stages + s * Gm::STAGE);
-                const uint32_t sB = st + Gm::A_BYTES, sBl = sB + TC_KG * Gm::PLANE;
-                for (int e = 0; e < cnt; ++e) {
-                    const int shz = e == 0 ? e01.y : e == 1 ? e01.w : e23.y;
-                    const uint32_t sA = st + (uint32_t)(e * 2 * TC_A_BYTES), sAl = sA + TC_A_BYTES;
-                    const uint64_t dAh = make_desc(sA, 128, TC_SBO), dAl = make_desc(sAl, 128, TC_SBO);
-                    const uint32_t acc0 = (i > 0 || e > 0) ? 1u : 0u;
+        const uint32_t fmt = BF16 ? 1u : 2u;
+        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(192 >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % TL_STAGES;
+            const uint32_t ph = (uint32_t)((i / TL_STAGES) & 1);
+            if (!mbar_wait(smem_u32(&full[s]), ph, tp.wait_limit, abort)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int ci = i % ncls;
+            const int4 hd = cls_s[3 * ci], e01 = cls_s[3 * ci + 1], e23 = cls_s[3 * ci + 2];
+            const int cnt = min(hd.w, TL_MAXOFF);
+            const uint32_t st = smem_u32(stages + s * Gm::STAGE);
+            const uint32_t sB = st + Gm::A_BYTES, sBl = sB + Gm::BOX_BYTES;
+            for (int e = 0; e < cnt; ++e) {
+                const int shz = e == 0 ? e01.y : e == 1 ? e01.w : e23.y;
+                const uint32_t sA = st + (uint32_t)(e * 2 * TC_A_BYTES), sAl = sA + TC_A_BYTES;
+                const uint64_t dAh = make_desc(sA, 128, TC_SBO), dAl = make_desc(sAl, 128, TC_SBO);
+                const uint32_t acc0 = (i > 0 || e > 0) ? 1u : 0u;
 #pragma unroll
-                    for (int hfl = 0; hfl < 2; ++hfl) {
-                        const uint32_t woff = (uint32_t)(((shz + TL_HALO) * Gm::ROW_Z + 192 * hfl) * 16);
-                        const uint64_t dBh = make_desc(sB + woff, Gm::PLANE, 128);
-                        const uint64_t dBl = make_desc(sBl + woff, Gm::PLANE, 128);
-                        const uint32_t td = tmem + (uint32_t)(192 * hfl);
-                        mma_issue<BF16>(td, dAh, dBh, idesc, acc0);
-                        mma_issue<BF16>(td, dAh, dBl, idesc, 1u);
-                        mma_issue<BF16>(td, dAl, dBh, idesc, 1u);
-                    }
+                for (int hfl = 0; hfl < 2; ++hfl) {
+                    const uint32_t woff = (uint32_t)(((shz + TL_HALO) * Gm::ROW_Z + 192 * hfl) * 16);
+                    const uint64_t dBh = make_desc(sB + woff, Gm::PLANE, 128);
+                    const uint64_t dBl = make_desc(sBl + woff, Gm::PLANE, 128);
+                    const uint32_t td = tmem + (uint32_t)(192 * hfl);
+                    mma_issue<BF16>(td, dAh, dBh, idesc, acc0);
+                    mma_issue<BF16>(td, dAh, dBl, idesc, 1u);
+                    mma_issue<BF16>(td, dAl, dBh, idesc, 1u);
                 }
-                mma_commit(smem_u32(&empty[s]));
             }
-            // drain: every MMA issued above has completed once this commit arrives
-            mma_commit(smem_u32(drain));
-            if (!mbar_wait_drain(smem_u32(drain), 0u)) ok = false;
+            mma_commit(smem_u32(&empty[s]));
         }
-    } else {
-        // ------------------------------- producers ---------------------------------
-        const int ptid = tid - 32;
-        int released = 0;  // stages this warp has released on full[]
+        // drain: every MMA issued above has completed once this commit arrives
+        mma_commit(smem_u32(drain));
+        if (!mbar_wait_drain(smem_u32(drain), 0u)) ok = false;
+    } else if (tid == 32) {
+        // ------------------------------- TMA producer -----------------------------
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_hi)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tm_lo)) : "memory");
         const unsigned char *Ahi = (const unsigned char *)tp.Ahi, *Alo = (const unsigned char *)tp.Alo;
-        const unsigned char *Bhi = (const unsigned char *)tp.Bhi, *Blo = (const unsigned char *)tp.Blo;
-        for (int i = 0; i < nk + TL_PF; ++i) {
-            if (i < nk) {
-                const int s = i % TL_STAGES;
-                if (i >= TL_STAGES &&
-                    !mbar_wait_warp(smem_u32(&empty[s]), (uint32_t)(((i / TL_STAGES) - 1) & 1), tp.wait_limit, abort)) {
-                    ok = false;
-                    break;
-                }
-                const int ch = i / ncls, ci = i - ch * ncls;
-                const int4 hd = cls_s[3 * ci], e01 = cls_s[3 * ci + 1], e23 = cls_s[3 * ci + 2];
-                const int cnt = min(hd.w, TL_MAXOFF);
-                const uint32_t st = smem_u32(stages + s * Gm::STAGE);
-                if (ptid == 0) {
-                    const uint32_t fb = smem_u32(&full[s]);
-                    *issued_sh = i + 1;
-                    mbar_expect_tx(fb, (uint32_t)(cnt * 2 * TC_A_BYTES));
-                    for (int e = 0; e < cnt; ++e) {
-                        const int tile = checked_index(e == 0 ? e01.x : e == 1 ? e01.z : e23.x, NT, tp.err);
-                        const uint32_t sA = st + (uint32_t)(e * 2 * TC_A_BYTES);
-                        bulk_g2s(sA, Ahi + ((size_t)tile * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
-                        bulk_g2s(sA + TC_A_BYTES, Alo + ((size_t)tile * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
-                    }
-                }
-                // the class's source lines: line l of this CTA is target line (px, py); its source
-                // is G[bpar][(px + shx) mod H][(py + shy) mod H][all Zp], staged as rows (Zp, l, comp)
-                const int bpar = hd.x, shx = hd.y, shy = hd.z;
-                const uint32_t sB = st + Gm::A_BYTES, sBl = sB + TC_KG * Gm::PLANE;
-                for (int v = ptid; v < Gm::CHUNKS; v += TC_THREADS) {
-                    const int kg = v % TC_KG;
-                    const int r = v / TC_KG;                    // staged row (Zp, l, comp)
-                    const int zp = r / Gm::ROW_Z, rl = r - zp * Gm::ROW_Z;
-                    const int l = rl / 3, comp = rl - 3 * l;
-                    const int L = line0 + l;
-                    const int px = L / H, py = L - (L / H) * H;
-                    const int X = (px + shx) & (H - 1), Y = (py + shy) & (H - 1);
-                    const int64_t srow = checked_index<int64_t>(
-                        (((int64_t)(ch * 8 + bpar) * H + X) * H + Y) * Gm::ROWS_LINE + zp * 3 + comp,
-                        (int64_t)nchunk * 8 * H * H * Gm::ROWS_LINE, tp.err);
-                    const size_t off = srow * TC_KBYTES + 16 * kg;
-                    const uint32_t dst = (uint32_t)(kg * Gm::PLANE + r * 16);
-                    cp_async16(sB + dst, Bhi + off);
-                    cp_async16(sBl + dst, Blo + off);
-                }
+        const int px = line0 / H, py0 = line0 - px * H;  // the CTA's lines: y = py0 .. py0 + LINES - 1
+        int issued = 0;
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % TL_STAGES;
+            if (i >= TL_STAGES &&
+                !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((i / TL_STAGES) - 1) & 1), tp.wait_limit, abort)) {
+                ok = false;
+                break;
             }
-            cp_async_commit();
-            if (i >= TL_PF) {
-                cp_async_wait<TL_PF>();
-                fence_proxy_async();
-                __syncwarp();
-                if ((tid & 31) == 0) mbar_arrive(smem_u32(&full[(i - TL_PF) % TL_STAGES]));
-                released = i - TL_PF + 1;
+            const int ch = i / ncls, ci = i - ch * ncls;
+            const int4 hd = cls_s[3 * ci], e01 = cls_s[3 * ci + 1], e23 = cls_s[3 * ci + 2];
+            const int cnt = min(hd.w, TL_MAXOFF);
+            const uint32_t st = smem_u32(stages + s * Gm::STAGE);
+            const uint32_t fb = smem_u32(&full[s]);
+            mbar_expect_tx(fb, (uint32_t)(cnt * 2 * TC_A_BYTES + Gm::B_BYTES));
+            for (int e = 0; e < cnt; ++e) {
+                const int tile = checked_index(e == 0 ? e01.x : e == 1 ? e01.z : e23.x, NT, tp.err);
+                const uint32_t sA = st + (uint32_t)(e * 2 * TC_A_BYTES);
+                bulk_g2s(sA, Ahi + ((size_t)tile * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
+                bulk_g2s(sA + TC_A_BYTES, Alo + ((size_t)tile * nchunk + ch) * TC_A_BYTES, TC_A_BYTES, fb);
             }
+            // the class's source lines: target line (px, py) reads G[bpar][(px + shx) mod H][py + shy]
+            // (periodic through the y halo) over all Zp; one box per hi/lo holds the LINES lines
+            const int X = checked_index((px + hd.y) & (H - 1), H, tp.err);
+            const int yp0 = checked_index(py0 + hd.z + TL_HALO, Gm::YP - Gm::LINES + 1, tp.err);
+            const int c4 = checked_index(ch * 8 + hd.x, nchunk * 8, tp.err);
+            const uint32_t sB = st + Gm::A_BYTES;
+            tensor_g2s_5d(sB, &tm_hi, yp0 * 24, 0, 0, X, c4, fb);
+            tensor_g2s_5d(sB + Gm::BOX_BYTES, &tm_lo, yp0 * 24, 0, 0, X, c4, fb);
+            issued = i + 1;
         }
-        // drain.  This thread's cp.async copies first.  Then the bulk copies of producer thread 0,
-        // which complete on full[]: once every producer warp has left its loop (named barrier),
-        // each warp arrives once on every stage thread 0 filled that it has not released (only
-        // after a give-up), so each such phase completes when its bytes land, and thread 0 waits
-        // for the last phase of every stage.
-        cp_async_wait<0>();
-        fence_proxy_async();
-        asm volatile("bar.sync 1, %0;" ::"n"(TC_THREADS) : "memory");
-        const int issued = *issued_sh;
-        __syncwarp();
-        if ((tid & 31) == 0)
-            for (int j = released; j < issued; ++j) mbar_arrive(smem_u32(&full[j % TL_STAGES]));
-        asm volatile("bar.sync 1, %0;" ::"n"(TC_THREADS) : "memory");
-        if (ptid == 0)
-            for (int j = issued > TL_STAGES ? issued - TL_STAGES : 0; j < issued; ++j)
-                if (!mbar_wait_drain(smem_u32(&full[j % TL_STAGES]), (uint32_t)((j / TL_STAGES) & 1))) ok = false;
+        // drain: a stage this thread filled completes its phase once its bytes land (one arrival,
+        // made with the expect_tx); wait for the last phase of every stage
+        for (int j = issued > TL_STAGES ? issued - TL_STAGES : 0; j < issued; ++j)
+            if (!mbar_wait_drain(smem_u32(&full[j % TL_STAGES]), (uint32_t)((j / TL_STAGES) & 1))) ok = false;
     }
-    // epilogue: the MMA thread has seen its drain commit arrive (all MMAs done) before this
-    // barrier; then warps 0..3 read TMEM lanes 32w..32w+31
+    // epilogue: the MMA thread has seen its drain commit arrive (all MMAs done) and the producer
+    // its copies land before this barrier; then warps 0..3 read TMEM lanes 32w..32w+31
     ok = __syncthreads_and((ok && !*abort) ? 1 : 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (ok && warp < 4) {
+    if (ok) {
         const int k = 32 * warp + (tid & 31);
         float *C = tp.C;
         const int gx = (g >> 2) & 1, gy = (g >> 1) & 1, gz = g & 1;
@@ -645,32 +630,33 @@ __global__ void __launch_bounds__(TL_THREADS, 1) k_m2l_lines(TcParams tp, const 
     }
 }
 
-// FP32 multipoles [cell][3][pc] of one level -> hi/lo parity grid G[b][X][Y][Zp][3][pc]
-// (h = n/2 cells per side and parity, Zp = Z + 2 with two periodic halo cells per side).
-// One thread per 8 consecutive coefficients (pc is a multiple of 8).
+// FP32 multipoles [cell][3][pc] of one level -> hi/lo parity grid
+// G[slice][b][X][kg][Zp][Yp][3][16 bytes] (h = n/2 cells per side and parity, Yp = Y + 2 and
+// Zp = Z + 2 with two periodic halo cells per side).  One thread per 8 consecutive
+// coefficients of one (cell, component) row (pc is a multiple of 8).
 template <typename TS>
 __global__ void k_split_grid(int n, int pc, const float *__restrict__ M, TS *__restrict__ hi, TS *__restrict__ lo)
 {
-    const int h = n >> 1, zp = h + 2 * TL_HALO, pv = pc >> 3;
-    const int64_t count = (int64_t)8 * h * h * zp * 3 * pv;
+    const int h = n >> 1, ext = h + 2 * TL_HALO, pv = pc >> 3;
+    const int64_t count = (int64_t)8 * h * ext * ext * 3 * pv;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     int64_t r = i;
     const int kv = (int)(r % pv); r /= pv;
     const int comp = (int)(r % 3); r /= 3;
-    const int Zp = (int)(r % zp); r /= zp;
-    const int Y = (int)(r % h); r /= h;
+    const int Zp = (int)(r % ext); r /= ext;
+    const int Yp = (int)(r % ext); r /= ext;
     const int X = (int)(r % h); r /= h;
     const int b = (int)r;
-    const int Z = (Zp - TL_HALO + h) & (h - 1);
+    const int Y = (Yp - TL_HALO + h) & (h - 1), Z = (Zp - TL_HALO + h) & (h - 1);
     const int64_t cell = ((int64_t)(2 * X + ((b >> 2) & 1)) * n + (2 * Y + ((b >> 1) & 1))) * n + (2 * Z + (b & 1));
     const float4 *src = (const float4 *)(M + (cell * 3 + comp) * pc + 8 * kv);
-    // destination: K slice of 32 bytes (16 BF16 / 8 TF32 coefficients) outermost
+    // 16-byte destination row of k-group kg of K slice ch (32 bytes: 16 BF16 / 8 TF32 coefficients)
     constexpr int VPS = TC_KBYTES / (8 * (int)sizeof(TS));  // 8-coefficient vectors per slice
     const int ch = kv / VPS, part = kv - ch * VPS;
-    const int64_t srow = i / pv;  // (b, X, Y, Zp, comp)
-    const int64_t nrows = count / pv;
-    const int64_t o = ((int64_t)ch * nrows + srow) * VPS + part;  // in 8-coefficient vectors
+    auto row16 = [&](int kg) -> int64_t {
+        return (((((int64_t)ch * 8 + b) * h + X) * 2 + kg) * ext + Zp) * ext * 3 + (int64_t)Yp * 3 + comp;
+    };
     const float4 a = src[0], c = src[1];
     const float v[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
     if constexpr (sizeof(TS) == 2) {
@@ -680,6 +666,7 @@ __global__ void k_split_grid(int n, int pc, const float *__restrict__ M, TS *__r
             hv[e] = __float2bfloat16_rn(v[e]);
             lv[e] = __float2bfloat16_rn(v[e] - __bfloat162float(hv[e]));
         }
+        const int64_t o = row16(part);
         reinterpret_cast<uint4 *>(hi)[o] = *reinterpret_cast<const uint4 *>(hv);
         reinterpret_cast<uint4 *>(lo)[o] = *reinterpret_cast<const uint4 *>(lv);
     } else {
@@ -689,11 +676,12 @@ __global__ void k_split_grid(int n, int pc, const float *__restrict__ M, TS *__r
             hv[e] = to_tf32_dev(v[e]);
             lv[e] = to_tf32_dev(v[e] - hv[e]);
         }
-        float4 *H = reinterpret_cast<float4 *>(hi) + 2 * o, *Lo = reinterpret_cast<float4 *>(lo) + 2 * o;
-        H[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
-        H[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
-        Lo[0] = make_float4(lv[0], lv[1], lv[2], lv[3]);
-        Lo[1] = make_float4(lv[4], lv[5], lv[6], lv[7]);
+        float4 *H = reinterpret_cast<float4 *>(hi), *Lo = reinterpret_cast<float4 *>(lo);
+        const int64_t o0 = row16(0), o1 = row16(1);
+        H[o0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        H[o1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+        Lo[o0] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        Lo[o1] = make_float4(lv[4], lv[5], lv[6], lv[7]);
     }
 }
 
@@ -753,7 +741,7 @@ size_t split_count(int level, int pc)
     const int64_t n = (int64_t)1 << level;
     if (!grid_level(level)) return (size_t)(n * n * n * 3 * pc);
     const int64_t h = n / 2;
-    return (size_t)(8 * h * h * (h + 2 * TL_HALO) * 3 * pc);
+    return (size_t)(8 * h * (h + 2 * TL_HALO) * (h + 2 * TL_HALO) * 3 * pc);
 }
 
 int launch_split(Ctx *c, int level, bool bf16)
@@ -815,6 +803,46 @@ void build_line_classes(const std::vector<int4> &kb, int off, int cnt, int g, st
 }
 
 namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point query (no link
+// against the driver library)
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// Tensor map of one hi or lo parity grid G[slice][b][X][kg][Zp][Yp][3][16 B] of a level with H
+// cells per side and parity, as 2-byte elements (the bytes are copied, whatever the type):
+// dims (innermost first) (Yp, component, 8 elements) flattened, Zp, kg, X, (slice, b).  The box
+// is LINES y-lines of all Zp and both k-groups of one (slice, b, X): in shared memory
+// [kg][Zp][line][component][16 B], the operand layout of the MMA.
+template <int H> bool encode_grid_map(CUtensorMap *map, const void *G, int nchunk)
+{
+    using Gm = TlGeom<H>;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t row = (cuuint64_t)Gm::YP * 3 * 16;  // bytes of one (kg, Zp) run of Yp rows
+    const cuuint64_t dims[5] = {(cuuint64_t)Gm::YP * 3 * 8, (cuuint64_t)Gm::ZP, 2, (cuuint64_t)H, (cuuint64_t)nchunk * 8};
+    const cuuint64_t strides[4] = {row, row * Gm::ZP, row * Gm::ZP * 2, row * Gm::ZP * 2 * H};
+    const cuuint32_t box[5] = {(cuuint32_t)Gm::BOX_X, (cuuint32_t)Gm::ZP, 2, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 5, const_cast<void *>(G), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <bool BF16, int H> int launch_lines(Ctx *c, int level, int R, const TcParams &tp0)
 {
     using Gm = TlGeom<H>;
@@ -832,9 +860,14 @@ template <bool BF16, int H> int launch_lines(Ctx *c, int level, int R, const TcP
         tp.kb_off[g] = c->cls_off[R][g];
         tp.kb_cnt[g] = c->cls_cnt[R][g];
     }
+    CUtensorMap mh, ml;
+    if (!encode_grid_map<H>(&mh, tp.Bhi, tp.nchunk) || !encode_grid_map<H>(&ml, tp.Blo, tp.nchunk)) {
+        c->last_error = "tensor-core M2L: cuTensorMapEncodeTiled failed";
+        return VFMM_ERR_CUDA;
+    }
     const int lines = H * H;  // target z-lines per parity
-    dim3 grid((unsigned)(lines / Gm::LINES), 8);
-    k_m2l_lines<BF16, H><<<grid, TL_THREADS, Gm::SMEM, c->stream>>>(tp, (const int4 *)c->cls.p);
+    dim3 grid(8, (unsigned)(lines / Gm::LINES));
+    k_m2l_lines<BF16, H><<<grid, TL_THREADS, Gm::SMEM, c->stream>>>(tp, (const int4 *)c->cls.p, mh, ml);
     VFMM_CUDA_CHECK_LAUNCH(c);
     return VFMM_OK;
 }
