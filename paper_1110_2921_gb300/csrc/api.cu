@@ -463,16 +463,25 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
             if ((rc = launch_root(c))) return rc;
         }
         cudaEventRecord(c->ev[5], st);
+        const bool tc = c->cfg.m2l_prec == VFMM_M2L_TF32X3 || c->cfg.m2l_prec == VFMM_M2L_BF16X3;
+        bool presplit = false;  // the leaf level's hi/lo split already issued
         if (overlap && VFMM_FORK_AT_M2L) {
+            // the leaf split in line, so that the first far-field launch beside the P2P is the
+            // leaf M2L itself
+            if (tc && VFMM_M2L_LEAF_FIRST && D >= 3) {
+                if ((rc = launch_split(c, D, c->cfg.m2l_prec == VFMM_M2L_BF16X3))) return rc;
+                presplit = true;
+            }
             fork();
             st = c->stream;
         }
-        const bool tc = c->cfg.m2l_prec == VFMM_M2L_TF32X3 || c->cfg.m2l_prec == VFMM_M2L_BF16X3;
-        for (int l = 1; l <= D; ++l) {
+        // the levels' M2L are independent; VFMM_M2L_LEAF_FIRST issues the leaf level first
+        for (int li = 0; li < D; ++li) {
+            const int l = VFMM_M2L_LEAF_FIRST ? D - li : li + 1;
             int Rl = (l == D) ? R : 1;
             if (tc && l >= 3) {
                 bool bf = c->cfg.m2l_prec == VFMM_M2L_BF16X3;
-                if ((rc = launch_split(c, l, bf))) return rc;
+                if (!(presplit && l == D) && (rc = launch_split(c, l, bf))) return rc;
                 if ((rc = launch_tc_m2l(c, l, Rl, bf))) return rc;
                 continue;
             }

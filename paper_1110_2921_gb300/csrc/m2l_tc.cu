@@ -13,25 +13,28 @@
 //
 // Two kernels share the operators and the pipeline mechanics:
 //   * k_m2l_lines (levels with 16 to 64 cells per side and parity, i.e. the large levels):
-//     128 target cells (whole z-lines) per CTA, offsets grouped by source line, one gathered
-//     source line serving all z shifts of its class (see the section below);
+//     128 target cells (whole z-lines) per CTA, offsets grouped by source line, one staged
+//     source line serving all z shifts of its class, every operand moved by TMA (see the
+//     section below);
 //   * k_m2l_tc (levels 3 and 4): 64 target cells per CTA, the B tile of every offset gathered
 //     row by row, the offset list split over several CTAs when the level has few cells.
 //
 // Mechanics (sm_103a): one elected thread of warp 0 issues tcgen05.mma (M = 128, N = 192,
 // K = 16 bf16 / 8 tf32 per instruction) from shared-memory descriptors in the canonical
-// no-swizzle K-major layout (8-row x 16-byte core matrices); producer warps gather the source
-// rows with cp.async and one producer thread moves the pre-tiled translation matrices with
-// TMA bulk copies (expect_tx on a per-stage transaction barrier); tcgen05.commit arrives on one
-// mbarrier per stage so a stage is refilled only after the MMAs that read it completed.
+// no-swizzle K-major layout (8-row x 16-byte core matrices); the pre-tiled translation
+// matrices arrive by TMA bulk copies (expect_tx on a per-stage transaction barrier), the
+// source rows by TMA tensor copies (k_m2l_lines) or cp.async gathers of producer warps
+// (k_m2l_tc); tcgen05.commit arrives on one mbarrier per stage so a stage is refilled only
+// after the MMAs that read it completed.
 // Every pipeline wait is bounded (TcParams.wait_limit tries).  A thread that gives up sets a
 // shared abort word, which every other pipeline wait polls, so the whole CTA stops issuing;
 // producer warps decide with one lane and leave their loop together.  Before TMEM is freed
-// the CTA drains its own asynchronous work: each producer thread waits for its cp.async
-// copies; every producer warp arrives on the stages producer thread 0 filled with bulk copies
-// that it had not released yet, and thread 0 waits for their phases (they complete once the
-// bytes land); the MMA thread commits once more and waits for that commit (every MMA it issued
-// has then completed).  The kernel then sets the timeout bit of the error word and returns.
+// the CTA drains its own asynchronous work: producer threads wait for their cp.async copies;
+// the thread that issued TMA copies waits for the phases of the stages it filled (they
+// complete once the bytes land; in k_m2l_tc every producer warp first arrives on the stages it
+// had not released); the MMA thread commits once more and waits for that commit (every MMA
+// it issued has then completed).  The kernel then sets the timeout bit of the error word and
+// returns.
 #include "common.cuh"
 #include "vfmm_internal.h"
 
@@ -463,8 +466,11 @@ __device__ __forceinline__ void tensor_g2s_5d(uint32_t dst, const CUtensorMap *m
         : "memory");
 }
 
+#ifndef VFMM_TL_MINB
+#define VFMM_TL_MINB 1
+#endif
 template <bool BF16, int H>
-__global__ void __launch_bounds__(TL_THREADS, 1)
+__global__ void __launch_bounds__(TL_THREADS, VFMM_TL_MINB)
     k_m2l_lines(TcParams tp, const int4 *__restrict__ cls, const __grid_constant__ CUtensorMap tm_hi,
                 const __grid_constant__ CUtensorMap tm_lo)
 {
@@ -644,8 +650,8 @@ __global__ void k_split_grid(int n, int pc, const float *__restrict__ M, TS *__r
     int64_t r = i;
     const int kv = (int)(r % pv); r /= pv;
     const int comp = (int)(r % 3); r /= 3;
+    const int Yp = (int)(r % ext); r /= ext;  // y inside z, as in the destination
     const int Zp = (int)(r % ext); r /= ext;
-    const int Yp = (int)(r % ext); r /= ext;
     const int X = (int)(r % h); r /= h;
     const int b = (int)r;
     const int Y = (Yp - TL_HALO + h) & (h - 1), Z = (Zp - TL_HALO + h) & (h - 1);

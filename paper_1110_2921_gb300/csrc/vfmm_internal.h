@@ -24,14 +24,23 @@ constexpr int TC_A_TILE = 128 * TC_KBYTES;  // bytes of one translation-matrix t
 // P2P beside the concurrent far field: VFMM_P2P_SHARED_BLOCKS > 0 runs it as a persistent grid
 // of that many one-warp blocks per SM (leaving room for far-field blocks on every SM), and
 // VFMM_FORK_AT_M2L = 1 runs the upward pass in line and forks only the M2L and the downward
-// pass.  Measured at 256^3 (step ms, every phase 73.7 ms in line): one block per task and the
-// fork before the P2M 72.9; fork at the M2L 73.1; persistent 16 or 20 blocks per SM 74-80
-// (the M2L then waits for the P2P).  Defaults: the first.
+// pass; VFMM_M2L_LEAF_FIRST = 1 issues the leaf level's M2L first (with the fork at the M2L
+// its hi/lo split then runs in line, so the first launch beside the P2P is the leaf M2L).
+// Measured at 256^3 with the cp.async source-line M2L (step ms, every phase 73.7 ms in line):
+// one block per task and the fork before the P2M 72.9; fork at the M2L 73.1; persistent 16 or
+// 20 blocks per SM 74-80 (the M2L then waits for the P2P).  With the TMA source-line M2L
+// (every phase 62.2 ms in line): default 60.7; fork at the M2L 60.85, and with the leaf level
+// first 60.9; leaf first alone 60.8; two M2L stages (with or without a 64-register cap, to leave
+// room for more P2P warps beside an M2L CTA) 61.6-61.8; fork, leaf first and a persistent P2P
+// of 20 blocks per SM 62.0 (no M2L CTA fits beside them).  Defaults: the first.
 #ifndef VFMM_P2P_SHARED_BLOCKS
 #define VFMM_P2P_SHARED_BLOCKS 0
 #endif
 #ifndef VFMM_FORK_AT_M2L
 #define VFMM_FORK_AT_M2L 0
+#endif
+#ifndef VFMM_M2L_LEAF_FIRST
+#define VFMM_M2L_LEAF_FIRST 0
 #endif
 
 // device error word bits
