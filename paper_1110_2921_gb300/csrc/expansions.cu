@@ -24,14 +24,19 @@ __constant__ double c_inv2m_d[PMAX + 1];
 template <typename T> __device__ __forceinline__ T sfac_t(int n, int m);
 template <> __device__ __forceinline__ float sfac_t<float>(int n, int m) { return c_sfac_f[n * (PMAX + 1) + m]; }
 template <> __device__ __forceinline__ double sfac_t<double>(int n, int m) { return c_sfac_d[n * (PMAX + 1) + m]; }
+// The same factors in global memory, for lookups whose (n, m) differs across a warp: constant
+// memory serialises a warp's loads from different addresses, the L1 serves them together.
+__device__ float g_sfac_f[(PMAX + 1) * (PMAX + 1)];
+__device__ double g_sfac_d[(PMAX + 1) * (PMAX + 1)];
+template <typename T> __device__ __forceinline__ T sfac_ld(int n, int m);
+template <> __device__ __forceinline__ float sfac_ld<float>(int n, int m) { return __ldg(&g_sfac_f[n * (PMAX + 1) + m]); }
+template <> __device__ __forceinline__ double sfac_ld<double>(int n, int m) { return __ldg(&g_sfac_d[n * (PMAX + 1) + m]); }
 template <typename T> __device__ __forceinline__ T rec_t(int n, int m);
 template <> __device__ __forceinline__ float rec_t<float>(int n, int m) { return c_rec_f[n * (PMAX + 1) + m]; }
 template <> __device__ __forceinline__ double rec_t<double>(int n, int m) { return c_rec_d[n * (PMAX + 1) + m]; }
 template <typename T> __device__ __forceinline__ T inv2m_t(int m);
 template <> __device__ __forceinline__ float inv2m_t<float>(int m) { return c_inv2m_f[m]; }
 template <> __device__ __forceinline__ double inv2m_t<double>(int m) { return c_inv2m_d[m]; }
-
-void set_l2p_tables();
 
 void set_constants(int)
 {
@@ -52,11 +57,12 @@ void set_constants(int)
     }
     cudaMemcpyToSymbol(c_sfac_f, sf, sizeof(sf));
     cudaMemcpyToSymbol(c_sfac_d, sd, sizeof(sd));
+    cudaMemcpyToSymbol(g_sfac_f, sf, sizeof(sf));
+    cudaMemcpyToSymbol(g_sfac_d, sd, sizeof(sd));
     cudaMemcpyToSymbol(c_rec_f, rf, sizeof(rf));
     cudaMemcpyToSymbol(c_rec_d, rd, sizeof(rd));
     cudaMemcpyToSymbol(c_inv2m_f, i2f, sizeof(i2f));
     cudaMemcpyToSymbol(c_inv2m_d, i2d, sizeof(i2d));
-    set_l2p_tables();
     set_carveouts_expansions();
     set_carveouts_p2p();
     set_carveouts_m2l();
@@ -576,27 +582,22 @@ int launch_root(Ctx *c)
 // gradients D^k U_a; each particle evaluates Y_a^b at its offset once and accumulates 12
 // table dot products.
 constexpr int L2P_BS = 64;   // one thread per particle of a 64-particle leaf
-constexpr int NCX_MAX = (PMAX + 1) * (PMAX + 2) / 2;
-__constant__ unsigned char c_cn[NCX_MAX], c_cm[NCX_MAX];  // complex index -> (n, m)
-
-void set_l2p_tables()
-{
-    unsigned char cn[NCX_MAX], cm[NCX_MAX];
-    int ci = 0;
-    for (int n = 0; n <= PMAX; ++n)
-        for (int m = 0; m <= n; ++m, ++ci) {
-            cn[ci] = (unsigned char)n;
-            cm[ci] = (unsigned char)m;
-        }
-    cudaMemcpyToSymbol(c_cn, cn, sizeof(cn));
-    cudaMemcpyToSymbol(c_cm, cm, sizeof(cm));
-}
 
 template <typename T> struct C2;
 template <> struct C2<float> { typedef float2 type; };
 template <> struct C2<double> { typedef double2 type; };
 
 __device__ __forceinline__ int cix(int n, int m) { return n * (n + 1) / 2 + m; }
+
+// inverse of cix: complex index -> (n, m), by arithmetic (the lanes of a warp decode different
+// indices, which a constant-memory table would serialise)
+__device__ __forceinline__ void cix_nm(int ci, int &n, int &m)
+{
+    int d = 0;
+    while ((d + 1) * (d + 2) / 2 <= ci) ++d;
+    n = d;
+    m = ci - d * (d + 1) / 2;
+}
 
 // complex coefficient (n, m) of a table in complex layout (m >= 0 stored), any m
 template <typename T>
@@ -662,35 +663,48 @@ __global__ void __launch_bounds__(L2P_BS) k_l2p(const typename V4<T>::type *__re
     const int b0 = ls[leaf], e0 = ls[leaf + 1];
     if (e0 <= b0) return;
     const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
-    for (int o = threadIdx.x; o < 3 * ncx; o += blockDim.x) {
-        int comp = o / ncx, ci = o - comp * ncx;
-        int n = c_cn[ci], m = c_cm[ci];
-        const T *src = Lc + (size_t)leaf * 3 * pc + comp * pc;
-        T sf = sfac_t<T>(n, m);
-        T2 v;
-        v.x = src[pk(n, m)] * sf;
-        v.y = m > 0 ? src[pk(n, m) + 1] * sf : T(0);
-        F[o] = v;
+    // each lane decodes its coefficient (n, m) once and fills every component / direction of it
+    const T *lsrc = Lc + (size_t)leaf * 3 * pc;
+    for (int ci = threadIdx.x; ci < ncx; ci += blockDim.x) {
+        int n, m;
+        cix_nm(ci, n, m);
+        const T sf = sfac_ld<T>(n, m);
+        const int k0 = pk(n, m);
+#pragma unroll
+        for (int comp = 0; comp < 3; ++comp) {
+            T2 v;
+            v.x = lsrc[comp * pc + k0] * sf;
+            v.y = m > 0 ? lsrc[comp * pc + k0 + 1] * sf : T(0);
+            F[comp * ncx + ci] = v;
+        }
     }
     __syncthreads();
     const int ng = p * (p + 1) / 2;  // entries of degree < p
-    for (int it = threadIdx.x; it < 3 * ng; it += blockDim.x) {
-        int ci = it % ng, a = it / ng;
-        int b = a == 2 ? 0 : a + 1, c = a == 0 ? 2 : a - 1;
-        T2 x1 = dcx<T>(F + c * ncx, p, b, c_cn[ci], c_cm[ci]);
-        T2 x2 = dcx<T>(F + b * ncx, p, c, c_cn[ci], c_cm[ci]);
-        T2 v;
-        v.x = x1.x - x2.x;
-        v.y = x1.y - x2.y;
-        U[a * ncx + ci] = v;
-        W[ci * 12 + a] = v;
+    for (int ci = threadIdx.x; ci < ng; ci += blockDim.x) {
+        int n, m;
+        cix_nm(ci, n, m);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int b = a == 2 ? 0 : a + 1, c = a == 0 ? 2 : a - 1;
+            T2 x1 = dcx<T>(F + c * ncx, p, b, n, m);
+            T2 x2 = dcx<T>(F + b * ncx, p, c, n, m);
+            T2 v;
+            v.x = x1.x - x2.x;
+            v.y = x1.y - x2.y;
+            U[a * ncx + ci] = v;
+            W[ci * 12 + a] = v;
+        }
     }
     __syncthreads();
     const int nh = (p - 1) * p / 2;  // entries of degree < p - 1
-    for (int it = threadIdx.x; it < 9 * nh; it += blockDim.x) {
-        int ci = it % nh, rest = it / nh;
-        int a = rest % 3, k = rest / 3;
-        W[ci * 12 + 3 + 3 * k + a] = dcx<T>(U + a * ncx, p - 1, k, c_cn[ci], c_cm[ci]);
+    // items (a, ci) spread over the lanes (45 entries alone would leave most lanes idle in a
+    // second pass); the three directions k unrolled
+    for (int it = threadIdx.x; it < 3 * nh; it += blockDim.x) {
+        const int a = (it >= nh) + (it >= 2 * nh), ci = it - a * nh;
+        int n, m;
+        cix_nm(ci, n, m);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) W[ci * 12 + 3 + 3 * k + a] = dcx<T>(U + a * ncx, p - 1, k, n, m);
     }
     __syncthreads();
     const T zx = (cx + T(0.5)) * w, zy = (cy + T(0.5)) * w, zz = (cz + T(0.5)) * w;
@@ -992,7 +1006,7 @@ __global__ void __launch_bounds__(DUAL_BS) k_dual_p2m(const typename V4<T>::type
     }
     if (k < pc) {
         T sc = 0;
-        if (k < nc) sc = T(0.0795774715459476679) * invw * invw * (m > 0 ? T(2) : T(1)) * sfac_t<T>(n, m);
+        if (k < nc) sc = T(0.0795774715459476679) * invw * invw * (m > 0 ? T(2) : T(1)) * sfac_ld<T>(n, m);
         T *out = Lam + (size_t)leaf * 3 * pc;
         out[k] = sc * a0;
         out[pc + k] = sc * a1;
@@ -1021,7 +1035,7 @@ __global__ void __launch_bounds__(DUAL_L2P_BS) k_dual_l2p(const typename V4<T>::
         const int comp = o / nc, k = o - comp * nc;
         int n, m, part;
         unpack_k(k, n, m, part);
-        mus[o] = Mu[(size_t)leaf * 3 * pc + comp * pc + k] * sfac_t<T>(n, m);
+        mus[o] = Mu[(size_t)leaf * 3 * pc + comp * pc + k] * sfac_ld<T>(n, m);
     }
     __syncthreads();
     const int cz = leaf & (nside - 1), cy = (leaf >> log2n) & (nside - 1), cx = leaf >> (2 * log2n);
