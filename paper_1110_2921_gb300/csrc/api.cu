@@ -479,7 +479,7 @@ int eval_impl(Ctx *c, const void *gamma, double sigma, void *u_out, void *s_out,
         for (int li = 0; li < D; ++li) {
             const int l = VFMM_M2L_LEAF_FIRST ? D - li : li + 1;
             int Rl = (l == D) ? R : 1;
-            if (tc && l >= 3) {
+            if (tc && l >= VFMM_TC_MIN_LEVEL) {
                 bool bf = c->cfg.m2l_prec == VFMM_M2L_BF16X3;
                 if (!(presplit && l == D) && (rc = launch_split(c, l, bf))) return rc;
                 if ((rc = launch_tc_m2l(c, l, Rl, bf))) return rc;

@@ -12,16 +12,27 @@
 
 namespace vfmm {
 
+// Box constants in the input's own precision, computed once on the host: FP64 arithmetic is
+// scarce on this part, and a division per thread of the key and leaf-sort kernels cost more
+// than the rest of their work.
+template <typename TIn> struct BoxConst {
+    TIn L, invL, scale;  // box, 1 / box, cells per unit length at the given level
+};
+template <typename TIn> BoxConst<TIn> box_const(double L, double cells)
+{
+    return BoxConst<TIn>{(TIn)L, (TIn)(1.0 / L), (TIn)(cells / L)};
+}
+
 template <typename TIn>
-__global__ void k_keys(int64_t n, const TIn *__restrict__ x, int nside, double L, int *__restrict__ keys,
+__global__ void k_keys(int64_t n, const TIn *__restrict__ x, int nside, BoxConst<TIn> bc, int *__restrict__ keys,
                        int *__restrict__ counts, int *__restrict__ err)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < n;
     int key = -1;
     if (active) {
-        // coordinates in the input's own precision (FP64 arithmetic is scarce on this part)
-        const TIn Lt = (TIn)L, invL = (TIn)(1.0 / L), scale = (TIn)((double)nside / L);
+        // coordinates in the input's own precision
+        const TIn Lt = bc.L, invL = bc.invL, scale = bc.scale;
         int c[3];
         bool finite = true;
         for (int d = 0; d < 3; ++d) {
@@ -144,7 +155,7 @@ __device__ __forceinline__ int f2ord(float f) { return __float_as_int(f); }  // 
 
 template <typename TIn, typename T>
 __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict__ tmpidx, const TIn *__restrict__ x,
-                            double L, int nside, int *__restrict__ perm, typename V4<T>::type *__restrict__ xs,
+                            BoxConst<TIn> bc, int nside, int *__restrict__ perm, typename V4<T>::type *__restrict__ xs,
                             float4 *__restrict__ bbox, int *__restrict__ oct_start, float4 *__restrict__ oct_box,
                             int *__restrict__ err)
 {
@@ -178,8 +189,8 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
     }
     const int cz = leaf % nside, cy = (leaf / nside) % nside, cx = leaf / (nside * nside);
     // the input's own precision, as for the leaf keys
-    const TIn Lt = (TIn)L, invL = (TIn)(1.0 / L);
-    const TIn s2 = (TIn)(2.0 * nside / L);
+    const TIn Lt = bc.L, invL = bc.invL;
+    const TIn s2 = bc.scale;  // octant cells (2 nside) per unit length
     int m = 1;
     while (m < cnt) m <<= 1;
     __syncthreads();
@@ -267,8 +278,8 @@ template <typename TIn, typename T> static int tree_impl(Ctx *c, const TIn *x)
     cudaMemsetAsync(c->fill.p, 0, nleaf * sizeof(int), st);
     cudaMemsetAsync(c->maxleaf.p, 0, sizeof(int), st);
     int nb = (int)((n + 255) / 256);
-    k_keys<TIn><<<nb, 256, 0, st>>>(n, x, c->nside, c->cfg.box, (int *)c->keys.p, (int *)c->counts.p,
-                                        (int *)c->err.p);
+    k_keys<TIn><<<nb, 256, 0, st>>>(n, x, c->nside, box_const<TIn>(c->cfg.box, (double)c->nside), (int *)c->keys.p,
+                                    (int *)c->counts.p, (int *)c->err.p);
     int nparts = (int)((nleaf + 1023) / 1024);
     int *start = (int *)c->leaf_start.p;
     int *part = (int *)c->scan_part.p;
@@ -298,7 +309,8 @@ template <typename TIn, typename T> static int leaf_sort_impl(Ctx *c, const TIn 
         attr[ai] = true;
     }
     int *start = (int *)c->leaf_start.p;
-    k_leaf_sort<TIn, T><<<(unsigned)c->nleaf, 64, sm, c->stream>>>(start, (int *)c->tmpidx.p, x, c->cfg.box, c->nside,
+    k_leaf_sort<TIn, T><<<(unsigned)c->nleaf, 64, sm, c->stream>>>(start, (int *)c->tmpidx.p, x,
+                                                                  box_const<TIn>(c->cfg.box, 2.0 * c->nside), c->nside,
                                                                   (int *)c->perm.p, (typename V4<T>::type *)c->xs.p,
                                                                   (float4 *)c->bbox.p, (int *)c->oct_start.p,
                                                                   (float4 *)c->oct_box.p, (int *)c->err.p);

@@ -39,6 +39,11 @@ constexpr int TC_A_TILE = 128 * TC_KBYTES;  // bytes of one translation-matrix t
 #ifndef VFMM_FORK_AT_M2L
 #define VFMM_FORK_AT_M2L 0
 #endif
+// lowest level whose M2L runs on the tensor cores (the levels below take the CUDA-core GEMM);
+// at 256^3 (step ms): 3 (default) 58.7, 4 58.9, 5 60.5
+#ifndef VFMM_TC_MIN_LEVEL
+#define VFMM_TC_MIN_LEVEL 3
+#endif
 #ifndef VFMM_M2L_LEAF_FIRST
 #define VFMM_M2L_LEAF_FIRST 0
 #endif
