@@ -921,16 +921,18 @@ int launch_tc_m2l(Ctx *c, int level, int R, bool bf16)
         }
         attr_set[bf16 ? 1 : 0] = true;
     }
-    // few CTAs (levels 3 and 4): split the offsets over about two CTAs per SM, partial tiles
-    // summed by a second pass in a fixed order
+    // few CTAs (levels 3 and 4): split the offsets over at most one wave of CTAs (two per SM;
+    // rounding up to more than one wave left a second wave of a few CTAs that doubled the time:
+    // 320 CTAs took 0.58 ms at 16^3 cells), partial tiles summed by a second pass in a fixed order
     dim3 grid((unsigned)(ncg / TC_CELLS), 8);
     const int64_t blocks = (int64_t)grid.x * grid.y;
     const int64_t count = (int64_t)n * n * n * 3 * c->pc;
+    const int64_t slots = 2 * (int64_t)std::max(c->sm_count, 1);
     int maxkb = 0;
     for (int g = 0; g < 8; ++g) maxkb = std::max(maxkb, tp.kb_cnt[g]);
     int ksplit = 1;
-    if (blocks < 304) {
-        ksplit = (int)std::min<int64_t>(maxkb, (304 + blocks - 1) / blocks);
+    if (blocks < slots) {
+        ksplit = (int)std::min<int64_t>(maxkb, slots / blocks);
         ksplit = (int)std::min<int64_t>(ksplit, (int64_t)(c->gemm_part.bytes / sizeof(float)) / count);
         // every slice keeps at least one offset
         while (ksplit > 1 && (int64_t)((maxkb + ksplit - 1) / ksplit) * (ksplit - 1) >= maxkb) --ksplit;
