@@ -130,12 +130,14 @@ def combine_ranks(ms, particles, steps, device=None):
     return ms_max, ws * particles * steps / (ms_max / 1e3)
 
 
-def p2p_work(x, L, depth, R, sigma, Rc=0, rho_cut=6.0):
+def p2p_work(x, L, depth, R, sigma, Rc=0, rho_cut=6.0, half_cull=True):
     """Pairs the P2P visits, split as the kernel splits them: by the gap d between the target
     leaf's box and each source octant's box.  In the R near rings d < 6.5 sigma -> smoothed
     kernel (61 flops), d >= 6.5 sigma -> singular kernel (42 flops); in the rings R+1..Rc
     (Gaussian-tail correction of the far field) d < rho_cut sigma -> smoothed minus singular
-    (61 flops), farther octants are skipped.  Returns (pairs, flops)."""
+    (61 flops), farther octants are skipped.  With half_cull the correction rings use the box
+    of each half of a warp's targets (ranks 0-31 and 32-63 of each 64-target chunk of a leaf
+    sorted by (octant, index)) instead of the leaf's box.  Returns (pairs, flops)."""
     import itertools
     import numpy as np
     ns = 1 << depth
@@ -160,6 +162,18 @@ def p2p_work(x, L, depth, R, sigma, Rc=0, rho_cut=6.0):
 
     cnt, lo, hi = boxes(key, nleaf)
     ocnt, olo, ohi = boxes(okey, 8 * nleaf)
+    if half_cull:
+        # rank of each particle in its leaf in the kernel's order (octant, caller index)
+        order = np.lexsort((np.arange(len(key)), okey))
+        first = np.searchsorted(key[order], key[order], side="left")
+        rank = np.empty(len(key), np.int64)
+        rank[order] = np.arange(len(key)) - first
+        grp = (rank // 64) * 2 + (rank % 64) // 32
+        G = int(grp.max()) + 1
+        hcnt, hlo, hhi = boxes(key * G + grp, G * nleaf)
+        hcnt = hcnt.reshape(ns, ns, ns, G)
+        hlo = hlo.reshape(ns, ns, ns, G, 3)
+        hhi = hhi.reshape(ns, ns, ns, G, 3)
     cnt = cnt.reshape(ns, ns, ns)
     lo = lo.reshape(ns, ns, ns, 3)
     hi = hi.reshape(ns, ns, ns, 3)
@@ -184,6 +198,17 @@ def p2p_work(x, L, depth, R, sigma, Rc=0, rho_cut=6.0):
             gap = np.maximum(0.0, np.maximum(slo - hi[..., d][..., None], lo[..., d][..., None] - shi))
             d2 += gap * gap
         pairs = cnt[..., None] * cn
+        if corr and half_cull:
+            for gi in range(G):
+                dh = np.zeros_like(cn)
+                for d in range(3):
+                    slo = olo[ix[0], ix[1], ix[2], :, d] + sh[d][..., None]
+                    shi = ohi[ix[0], ix[1], ix[2], :, d] + sh[d][..., None]
+                    gap = np.maximum(0.0, np.maximum(slo - hhi[..., gi, d][..., None], hlo[..., gi, d][..., None] - shi))
+                    dh += gap * gap
+                hp = hcnt[..., gi][..., None] * cn
+                p_s += float(hp[dh < d2_cut].sum())
+            continue
         if corr:
             p_s += float(pairs[d2 < d2_cut].sum())
             continue

@@ -266,9 +266,17 @@ __device__ __forceinline__ void pair3(const P3Const &k, float xi0, float xi1, fl
 #define VFMM_P3_SPLIT 0
 #endif
 constexpr int P3_SPLIT = VFMM_P3_SPLIT;
+// VFMM_P3_HALF_CULL = 1: the ring-2 correction is culled per (half of the warp's targets, source
+// octant) instead of per (target leaf, source octant).  The two targets of a lane are q = 0 (the
+// first 32 of the chunk) and q = 1 (the next 32); the leaf's particles are sorted by octant, so
+// on a regular distribution the halves are the leaf's two x-halves.
+#ifndef VFMM_P3_HALF_CULL
+#define VFMM_P3_HALF_CULL 1
+#endif
 constexpr int P3_THREADS = 32;                            // one warp per target leaf chunk
 constexpr int P3_TPT = P3_SPLIT ? 4 : VFMM_P3_TPT;        // targets per lane
 constexpr int P3_LANES = P3_SPLIT ? 16 : 32;              // lanes that share one source
+constexpr bool P3_HALVES = VFMM_P3_HALF_CULL && !P3_SPLIT && P3_TPT == 2;
 constexpr int P3_TARGETS = P3_LANES * P3_TPT;             // targets per block
 constexpr int P3_TILE = 64;      // staged sources
 constexpr int P3_UNROLL = VFMM_P3_UNROLL;
@@ -288,6 +296,22 @@ __device__ __forceinline__ void tile3(const P3Const &k, const float (&xi)[P3_TPT
         const float4 xj = src[j].x, gj = src[j].g, cj = src[j].c;
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) pair3<MODE>(k, xi[q][0], xi[q][1], xi[q][2], gi[q][0], gi[q][1], gi[q][2], xj, gj, cj, acc[q]);
+    }
+}
+
+// The general loop for the targets of one half only (QM = 1: q = 0, QM = 2: q = 1): a ring-2
+// octant that only one half of the warp's targets comes within rho_cut sigma of.
+template <int MODE, int QM>
+__device__ __forceinline__ void tile3q(const P3Const &k, const float (&xi)[P3_TPT][3], const float (&gi)[P3_TPT][3],
+                                       const Src3 *src, int j0, int j1, Acc3 (&acc)[P3_TPT])
+{
+#pragma unroll P3_UNROLL
+    for (int j = j0; j < j1; ++j) {
+        const float4 xj = src[j].x, gj = src[j].g, cj = src[j].c;
+#pragma unroll
+        for (int q = 0; q < P3_TPT; ++q)
+            if ((QM >> q) & 1)
+                pair3<MODE>(k, xi[q][0], xi[q][1], xi[q][2], gi[q][0], gi[q][1], gi[q][2], xj, gj, cj, acc[q]);
     }
 }
 
@@ -402,6 +426,7 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
 {
     __shared__ Src3 src[P3_TILE];
     __shared__ int ost[9];
+    __shared__ float hbox[2][6];  // boxes (true units) of the two target halves: lo xyz, hi xyz
     const float s = kc.s;
     // tasks = (leaf, chunk of P3_TARGETS targets); the grid is either one block per task or a
     // persistent grid that strides over them
@@ -426,7 +451,25 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
             gi[q][0] = g.x;
             gi[q][1] = g.y;
             gi[q][2] = g.z;
+            if (P3_HALVES) {
+                // box of this half's targets (empty halves give lo > hi, so no octant is near)
+                const bool act = ti < te;
+                float b[6] = {act ? x.x : 3e38f, act ? x.y : 3e38f, act ? x.z : 3e38f,
+                              act ? x.x : -3e38f, act ? x.y : -3e38f, act ? x.z : -3e38f};
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        b[d] = fminf(b[d], __shfl_xor_sync(0xffffffffu, b[d], off));
+                        b[3 + d] = fmaxf(b[3 + d], __shfl_xor_sync(0xffffffffu, b[3 + d], off));
+                    }
+                __syncwarp();
+                if ((threadIdx.x & 31) == 0)
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) hbox[q & 1][d] = b[d];
+            }
         }
+        if (P3_HALVES) __syncwarp();
         Acc3 acc[P3_TPT];
 #pragma unroll
         for (int q = 0; q < P3_TPT; ++q) acc[q] = Acc3{0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -451,7 +494,7 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
         const int n_off = (hi[0] - lo[0] + 1) * n1 * n2;
         const int lane = threadIdx.x & 31;
         for (int idx0 = 0; idx0 < n_off; idx0 += 4) {
-            int my_mode = 4;
+            int my_mode = 4, my_q = 3;  // my_q: the target halves an octant of mode 3 is near
             {
                 const int idx = idx0 + (lane >> 3), o = lane & 7;
                 if (idx < n_off) {
@@ -474,16 +517,31 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
                         const float d2 = gx * gx + gy * gy + gz * gz;
                         my_mode = corr ? (d2 < kc.d2_cut ? 3 : 4)
                                        : (d2 >= kc.d2_singular ? 2 : (d2 >= kc.d2_series ? 1 : 0));
+                        if (P3_HALVES && my_mode == 3) {
+                            my_q = 0;
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const float hx = fmaxf(0.f, fmaxf(slo.x + shx - hbox[h][3], hbox[h][0] - shi.x - shx));
+                                const float hy = fmaxf(0.f, fmaxf(slo.y + shy - hbox[h][4], hbox[h][1] - shi.y - shy));
+                                const float hz = fmaxf(0.f, fmaxf(slo.z + shz - hbox[h][5], hbox[h][2] - shi.z - shz));
+                                if (hx * hx + hy * hy + hz * hz < kc.d2_cut) my_q |= 1 << h;
+                            }
+                            if (my_q == 0) my_mode = 4;
+                        }
                     }
                 }
             }
             const unsigned b0 = __ballot_sync(0xffffffffu, my_mode & 1), b1 = __ballot_sync(0xffffffffu, my_mode & 2),
                            b2 = __ballot_sync(0xffffffffu, my_mode & 4);
+            // halves of the warp's targets that a mode-3 octant is near (both for every other mode)
+            const unsigned bh0 = P3_HALVES ? __ballot_sync(0xffffffffu, my_q & 1) : 0xffffffffu,
+                           bh1 = P3_HALVES ? __ballot_sync(0xffffffffu, my_q & 2) : 0xffffffffu;
             for (int li = 0; li < 4; ++li) {
                 const int idx = idx0 + li;
                 if (idx >= n_off) break;
                 const unsigned m0 = (b0 >> (8 * li)) & 0xFFu, m1 = (b1 >> (8 * li)) & 0xFFu,
-                               m2 = (b2 >> (8 * li)) & 0xFFu;
+                               m2 = (b2 >> (8 * li)) & 0xFFu, h0 = (bh0 >> (8 * li)) & 0xFFu,
+                               h1 = (bh1 >> (8 * li)) & 0xFFu;
                 if (m2 == 0xFFu && (m0 | m1) == 0u) continue;  // all eight octants: nothing to add
                 const int ox = lo[0] + idx / (n1 * n2), oy = lo[1] + (idx / n2) % n1, oz = lo[2] + idx % n2;
                 const int nx = cx + ox, ny = cy + oy, nz = cz + oz;
@@ -509,15 +567,25 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
                     }
                     __syncwarp();
                     const int c0 = s0 - sb, c1 = c0 + cnt;
-                    // runs of consecutive octants with the same inner loop
+                    // runs of consecutive octants with the same inner loop (mode, and for mode 3
+                    // the target halves it serves)
+                    auto run_key = [&](int oo) {
+                        return (int)(((m0 >> oo) & 1u) | (((m1 >> oo) & 1u) << 1) | (((m2 >> oo) & 1u) << 2) |
+                                     (((h0 >> oo) & 1u) << 3) | (((h1 >> oo) & 1u) << 4));
+                    };
                     int o = 0;
                     while (o < 8) {
-                        const int mode = (int)(((m0 >> o) & 1u) | (((m1 >> o) & 1u) << 1) | (((m2 >> o) & 1u) << 2));
+                        const int key = run_key(o);
+                        const int mode = key & 7, qm = key >> 3;
                         int o2 = o + 1;
-                        while (o2 < 8 && (int)(((m0 >> o2) & 1u) | (((m1 >> o2) & 1u) << 1) | (((m2 >> o2) & 1u) << 2)) == mode)
-                            ++o2;
+                        while (o2 < 8 && run_key(o2) == key) ++o2;
                         const int j0 = max(ost[o], c0) - c0, j1 = min(ost[o2], c1) - c0;
-                        if (VFMM_P3_FULLTILE > 0 && !P3_SPLIT && j0 == 0 && j1 == P3_TILE && (mode == 1 || mode == 3)) {
+                        if (mode == 3 && qm != 3) {
+                            if (j0 < j1) {
+                                if (qm == 1) tile3q<3, 1>(kc, xi, gi, src, j0, j1, acc);
+                                else tile3q<3, 2>(kc, xi, gi, src, j0, j1, acc);
+                            }
+                        } else if (VFMM_P3_FULLTILE > 0 && !P3_SPLIT && j0 == 0 && j1 == P3_TILE && (mode == 1 || mode == 3)) {
                             if (mode == 1) tile3_full<1>(kc, xi, gi, src, acc);
                             else tile3_full<3>(kc, xi, gi, src, acc);
                         } else if (j0 < j1) {

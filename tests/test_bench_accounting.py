@@ -54,3 +54,55 @@ def test_profiled_traffic_scales_with_particles(tmp_path, monkeypatch):
         return
     t8 = bench.profiled_traffic("k_p2p_f32", ["p2p.cu"], 2 ** 24)
     assert np.isclose(t8, 8 * t)
+
+
+def test_correction_ring_half_cull_matches_brute_force():
+    # ring 2 culled per (half of a leaf's 64 targets, source octant): on the 16^3 lattice the
+    # halves are the leaf's two x-slabs, and a ring-2 octant on the +x side with rho_cut = 5.5
+    # is near only the upper slab.  The count equals a direct loop over (target leaf, half,
+    # ring-2 leaf, octant) with the same box gaps, and lies between the uncorrected count and
+    # the count with the whole leaf's box
+    n = 16
+    x = wl.lattice_positions(n)
+    h = 2 * math.pi / n
+    L = 2 * math.pi
+    base = bench.p2p_work(x, L, 2, 1, h, Rc=0, rho_cut=5.0)
+    leafbox = bench.p2p_work(x, L, 2, 1, h, Rc=2, rho_cut=5.5, half_cull=False)
+    half = bench.p2p_work(x, L, 2, 1, h, Rc=2, rho_cut=5.5, half_cull=True)
+    assert base[0] < half[0] < leafbox[0]
+    # direct count
+    ns, w = 4, L / 4
+    xf = np.mod(x, L).astype(np.float32).astype(np.float64)
+    cell = np.clip((xf / w).astype(int), 0, ns - 1)
+    octv = np.clip((xf / (w / 2)).astype(int) - 2 * cell, 0, 1)
+    leaf = (cell[:, 0] * ns + cell[:, 1]) * ns + cell[:, 2]
+    okey = octv[:, 0] * 4 + octv[:, 1] * 2 + octv[:, 2]
+    cut2 = (5.5 * h) ** 2
+    total = 0
+    for lf in range(ns ** 3):
+        idx = np.nonzero(leaf == lf)[0]
+        idx = idx[np.lexsort((idx, okey[idx]))]         # the kernel's order within the leaf
+        halves = [idx[:32], idx[32:64]]
+        c = np.array([lf // (ns * ns), (lf // ns) % ns, lf % ns])
+        for t in np.ndindex(5, 5, 5):
+            o = np.array(t) - 2
+            if np.abs(o).max() <= 1:
+                continue
+            nb = c + o
+            src = (np.mod(nb[0], ns) * ns + np.mod(nb[1], ns)) * ns + np.mod(nb[2], ns)
+            shift = np.floor_divide(nb, ns) * L
+            sidx = np.nonzero(leaf == src)[0]
+            for oc in range(8):
+                so = sidx[okey[sidx] == oc]
+                if len(so) == 0:
+                    continue
+                slo = xf[so].min(0) + shift
+                shi = xf[so].max(0) + shift
+                for hv in halves:
+                    if len(hv) == 0:
+                        continue
+                    tlo, thi = xf[hv].min(0), xf[hv].max(0)
+                    gap = np.maximum(0.0, np.maximum(slo - thi, tlo - shi))
+                    if float((gap * gap).sum()) < cut2:
+                        total += len(hv) * len(so)
+    assert half[0] - base[0] == total
