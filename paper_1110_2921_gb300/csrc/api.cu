@@ -692,6 +692,7 @@ int vfmm_create(const vfmm_config *cfg, vfmm_handle *out)
     for (int i = 0; i < 12; ++i) {
         if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
             cudaGetLastError();
+            for (int j = 0; j < i; ++j) cudaEventDestroy(c->ev[j]);
             delete h;
             return VFMM_ERR_CUDA;
         }
