@@ -86,14 +86,16 @@ def test_line_levels_match_fp32_m2l_128cubed(m2l):
     assert eu < 4e-5 and es < 4e-5
 
 
-def test_line_levels_deep_tree_match_fp32_m2l():
+@pytest.mark.parametrize("m2l", ["bf16x3", "tf32x3"])
+def test_line_levels_deep_tree_match_fp32_m2l(m2l):
     # 64^3 particles on a depth-7 tree: levels 5, 6, 7 (16, 32, 64 cells per side and parity)
-    # all take the source-line kernel; sparse leaves, one near ring, correction ring 2
+    # all take the source-line kernel (its TMA tensor boxes of 2-byte and of 4-byte operands);
+    # sparse leaves, one near ring (rho_cut sigma within one leaf width: no correction ring)
     f = wl.make_vortex_lattice(64, 8, 1)
     kw = dict(p=10, depth=7, periodic_levels=1, rho_cut=2.0)
     sig = 0.25 * f["sigma"]
     u32, s32, _ = run_fmm(f["x"], f["alpha"], sig, m2l="fp32", **kw)
-    u, s, info = run_fmm(f["x"], f["alpha"], sig, m2l="bf16x3", **kw)
+    u, s, info = run_fmm(f["x"], f["alpha"], sig, m2l=m2l, **kw)
     eu, es = rel_l2(u, u32), rel_l2(s, s32)
     print(info, eu, es)
     assert info["depth"] == 7
