@@ -148,9 +148,12 @@ __global__ void k_scatter(int64_t n, const int *__restrict__ keys, const int *__
     tmpidx[pos] = (int)i;
 }
 
-// One block per leaf: sort the leaf's particles by (octant of the leaf, caller index) with a
-// bitonic sort in shared memory, then write the permutation, the wrapped sorted positions,
-// the leaf box, and the start and box of each octant (used to pick the P2P inner loop).
+constexpr int LEAF_RANK_MAX = 128;  // leaves up to this size are sorted by ranking, larger ones bitonically
+
+// One block per leaf: sort the leaf's particles by (octant of the leaf, caller index) in shared
+// memory (by ranking for small leaves, else a bitonic sort), then write the permutation, the
+// wrapped sorted positions, the leaf box, and the start and box of each octant (used to pick
+// the P2P inner loop).
 __device__ __forceinline__ int f2ord(float f) { return __float_as_int(f); }  // positions are >= 0
 
 template <typename TIn, typename T>
@@ -211,30 +214,15 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
         s[k] = key;
     }
     __syncthreads();
-    for (int size = 2; size <= m; size <<= 1)
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int k = threadIdx.x; k < m; k += blockDim.x) {
-                int q = k ^ stride;
-                if (q > k) {
-                    bool up = (k & size) == 0;
-                    unsigned long long a = s[k], c = s[q];
-                    if ((a > c) == up) {
-                        s[k] = c;
-                        s[q] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-        unsigned long long key = s[k];
+    // one sorted element: permutation, wrapped position, octant count and box
+    auto emit = [&](int pos, unsigned long long key) {
         int i = (int)(unsigned)(key & 0xffffffffull);
         int o = (int)(key >> 32);
-        perm[b + k] = i;
+        perm[b + pos] = i;
         T c0 = (T)wrap_coord<TIn>(x[3 * (int64_t)i + 0], Lt, invL);
         T c1 = (T)wrap_coord<TIn>(x[3 * (int64_t)i + 1], Lt, invL);
         T c2 = (T)wrap_coord<TIn>(x[3 * (int64_t)i + 2], Lt, invL);
-        xs[b + k] = make_v4<T>(c0, c1, c2, T(0));
+        xs[b + pos] = make_v4<T>(c0, c1, c2, T(0));
         // boxes of the FP32-rounded positions the P2P kernel sees
         float cf[3] = {(float)c0, (float)c1, (float)c2};
         atomicAdd(&ocnt[o], 1);
@@ -242,6 +230,33 @@ __global__ void k_leaf_sort(const int *__restrict__ start, const int *__restrict
             atomicMin(&omin[o][d], f2ord(cf[d]));
             atomicMax(&omax[o][d], f2ord(cf[d]));
         }
+    };
+    if (cnt <= LEAF_RANK_MAX) {
+        // the keys are distinct (the caller index is the low word): an element's place is the
+        // number of smaller keys, found by one pass over the leaf's keys without a barrier
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            const unsigned long long key = s[k];
+            int r = 0;
+            for (int j = 0; j < cnt; ++j) r += s[j] < key ? 1 : 0;
+            emit(r, key);
+        }
+    } else {
+        for (int size = 2; size <= m; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int k = threadIdx.x; k < m; k += blockDim.x) {
+                    int q = k ^ stride;
+                    if (q > k) {
+                        bool up = (k & size) == 0;
+                        unsigned long long a = s[k], c = s[q];
+                        if ((a > c) == up) {
+                            s[k] = c;
+                            s[q] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) emit(k, s[k]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
