@@ -5,6 +5,7 @@ import os
 import sys
 
 import numpy as np
+import pytest
 
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import bench  # noqa: E402
@@ -56,15 +57,24 @@ def test_profiled_traffic_scales_with_particles(tmp_path, monkeypatch):
     assert np.isclose(t8, 8 * t)
 
 
-def test_correction_ring_half_cull_matches_brute_force():
-    # ring 2 culled per (half of a leaf's 64 targets, source octant): on the 16^3 lattice the
-    # halves are the leaf's two x-slabs, and a ring-2 octant on the +x side with rho_cut = 5.5
-    # is near only the upper slab.  The count equals a direct loop over (target leaf, half,
+def _half_cull_cases():
+    n = 16
+    h = 2 * math.pi / n
+    lat = wl.lattice_positions(n)
+    # random positions: leaves of 30 to 100 particles, so some leaves hold two 64-target chunks
+    rnd = np.random.default_rng(7).uniform(0, 2 * math.pi, (n ** 3, 3))
+    return [("lattice", lat, h), ("random", rnd, h)]
+
+
+@pytest.mark.parametrize("case", ["lattice", "random"])
+def test_correction_ring_half_cull_matches_brute_force(case):
+    # ring 2 culled per (half of a 64-target chunk of a leaf, source octant): on the 16^3
+    # lattice the halves are the leaf's two x-slabs, and a ring-2 octant on the +x side with
+    # rho_cut = 5.5 is near only the upper slab; random positions add leaves of more than 64
+    # particles (two chunks).  The count equals a direct loop over (target leaf, chunk, half,
     # ring-2 leaf, octant) with the same box gaps, and lies between the uncorrected count and
     # the count with the whole leaf's box
-    n = 16
-    x = wl.lattice_positions(n)
-    h = 2 * math.pi / n
+    name, x, h = [c for c in _half_cull_cases() if c[0] == case][0]
     L = 2 * math.pi
     base = bench.p2p_work(x, L, 2, 1, h, Rc=0, rho_cut=5.0)
     leafbox = bench.p2p_work(x, L, 2, 1, h, Rc=2, rho_cut=5.5, half_cull=False)
@@ -82,7 +92,7 @@ def test_correction_ring_half_cull_matches_brute_force():
     for lf in range(ns ** 3):
         idx = np.nonzero(leaf == lf)[0]
         idx = idx[np.lexsort((idx, okey[idx]))]         # the kernel's order within the leaf
-        halves = [idx[:32], idx[32:64]]
+        halves = [idx[k:k + 32] for k in range(0, len(idx), 32)]  # chunks of 64, halves of 32
         c = np.array([lf // (ns * ns), (lf // ns) % ns, lf % ns])
         for t in np.ndindex(5, 5, 5):
             o = np.array(t) - 2
