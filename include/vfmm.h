@@ -229,8 +229,10 @@ int vfmm_get_timings(vfmm_handle h, double *ms_per_phase, int nphase);
 /* Tree facts: out[0] = depth D, out[1] = near rings R used by the last evaluation,
  * out[2] = leaves per side, out[3] = maximum particles in one leaf, out[4] = particles,
  * out[5] = CUDA kernels launched by the last vfmm_build_tree plus the evaluations since,
- * out[6] = outer ring of the Gaussian-tail correction in the last evaluation (0 = none).
- * Writes min(nout, 7) values. */
+ * out[6] = outer ring of the Gaussian-tail correction in the last evaluation (0 = none),
+ * out[7] = source-target pairs of real targets computed by the last FP32 near-field launch, as
+ * counted on the device by a library built with -DVFMM_CHECK=1 (waits for the handle's stream;
+ * 0 in the default build).  Writes min(nout, 8) values. */
 int vfmm_get_tree_info(vfmm_handle h, int64_t *out, int nout);
 
 /* Peak-rate probes, the measured denominators of the roofline fractions (measurement only;

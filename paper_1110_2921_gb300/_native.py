@@ -203,10 +203,11 @@ def vfmm_get_timings(h):
 
 
 def vfmm_get_tree_info(h):
-    buf = (ctypes.c_int64 * 7)()
-    check(lib().vfmm_get_tree_info(h, buf, 7), "vfmm_get_tree_info", h)
+    buf = (ctypes.c_int64 * 8)()
+    check(lib().vfmm_get_tree_info(h, buf, 8), "vfmm_get_tree_info", h)
     return {"depth": buf[0], "near_rings": buf[1], "leaves_per_side": buf[2],
-            "max_leaf": buf[3], "n": buf[4], "launches": buf[5], "correction_rings": buf[6]}
+            "max_leaf": buf[3], "n": buf[4], "launches": buf[5], "correction_rings": buf[6],
+            "p2p_pairs_checked": buf[7]}
 
 
 def vfmm_probe_peak(kind, reps, stream_ptr, err_ptr=None):

@@ -1012,8 +1012,13 @@ int vfmm_get_tree_info(vfmm_handle h, int64_t *out, int nout)
 {
     if (!h || !out) return VFMM_ERR_ARG;
     Ctx *c = &h->c;
-    int64_t v[7] = {c->depth, c->last_R, c->nside, c->max_leaf, c->n, c->launches, c->last_Rc};
-    for (int i = 0; i < nout && i < 7; ++i) out[i] = v[i];
+    int64_t pairs = 0;
+    if (VFMM_CHECK && nout > 7) {
+        cudaStreamSynchronize(c->stream);
+        pairs = p2p_pairs_read();
+    }
+    int64_t v[8] = {c->depth, c->last_R, c->nside, c->max_leaf, c->n, c->launches, c->last_Rc, pairs};
+    for (int i = 0; i < nout && i < 8; ++i) out[i] = v[i];
     return VFMM_OK;
 }
 

@@ -402,6 +402,12 @@ constexpr int P2P_BS = 64;
 constexpr float INV_4PI_F = 0.0795774715459476679f;
 constexpr double INV_4PI_D = 0.0795774715459476679;
 
+#if VFMM_CHECK
+// checked build: source-target pairs the FP32 P2P computed for real targets (the accounting
+// behind the benchmark's roofline, compared with its host-side count by a test)
+__device__ unsigned long long g_p2p_pairs;
+#endif
+
 #ifndef VFMM_P3_MINB
 #if VFMM_P3_SPLIT
 #define VFMM_P3_MINB 20  // 20 one-warp blocks per SM (102 registers: four targets per lane)
@@ -580,6 +586,15 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
                         int o2 = o + 1;
                         while (o2 < 8 && run_key(o2) == key) ++o2;
                         const int j0 = max(ost[o], c0) - c0, j1 = min(ost[o2], c1) - c0;
+#if VFMM_CHECK
+                        if (!P3_SPLIT && mode < 4 && j0 < j1 && (threadIdx.x & 31) == 0) {
+                            // targets of this chunk in each half that the run serves
+                            const int na0 = min(max(te - t0, 0), P3_LANES), na1 = min(max(te - t0 - P3_LANES, 0), P3_LANES);
+                            const int qmr = mode == 3 ? qm : 3;
+                            const int nt = ((qmr & 1) ? na0 : 0) + ((qmr & 2) ? na1 : 0);
+                            atomicAdd(&g_p2p_pairs, (unsigned long long)(j1 - j0) * (unsigned long long)nt);
+                        }
+#endif
                         if (mode == 3 && qm != 3) {
                             if (j0 < j1) {
                                 if (qm == 1) tile3q<3, 1>(kc, xi, gi, src, j0, j1, acc);
@@ -706,9 +721,30 @@ __global__ void __launch_bounds__(P2P_BS) k_p2p_f64(const dvec4 *__restrict__ xs
 
 void set_carveouts_p2p() { prefer_max_shared(k_p2p_f32); }
 
+// Pair counter of the checked build (0 in the default build): reset before a launch, read after.
+int64_t p2p_pairs_read()
+{
+#if VFMM_CHECK
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_p2p_pairs, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (int64_t)v;
+#else
+    return 0;
+#endif
+}
+
 int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void *sfar, void *u_out, void *s_out,
                int direct_K)
 {
+#if VFMM_CHECK
+    {
+        const unsigned long long zero = 0;
+        cudaMemcpyToSymbolAsync(g_p2p_pairs, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, c->stream);
+    }
+#endif
     int log2n = 0;
     while ((1 << log2n) < c->nside) ++log2n;
     int chunks = (c->max_leaf + P2P_BS - 1) / P2P_BS;

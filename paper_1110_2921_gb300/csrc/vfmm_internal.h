@@ -215,6 +215,7 @@ int launch_adjoint_combine(Ctx *c, const void *G1, const void *w, const void *G2
 // direct_K >= 0: direct sum over every leaf of the (2K+1)^3 image boxes; -1: the FMM near field (R rings)
 int launch_p2p(Ctx *c, int R, int Rc, double sigma, const void *ufar, const void *sfar, void *u_out,
                void *s_out, int direct_K);
+int64_t p2p_pairs_read();  // checked build: pairs of the last FP32 P2P launch (0 otherwise)
 int launch_tc_m2l(Ctx *c, int level, int R, bool bf16);  // R: near rings excluded at this level
 // classes of one parity's M2L list for the source-line kernel: per class three int4
 // {source parity, x shift, y shift, count}, {tile, z shift, tile, z shift} x 2
