@@ -32,11 +32,12 @@
  *    memory in vfmm_create / vfmm_build_tree / the first evaluation of a size.
  *  - Work is enqueued on cfg.stream (a cudaStream_t; NULL = legacy default stream).
  *    vfmm_eval_* is asynchronous: device-side errors (e.g. a leaf overflow) are
- *    reported by the next vfmm_sync().  vfmm_build_tree synchronises the stream twice (the
- *    largest leaf sizes the per-leaf sort; the occupancy check).  With concurrent_far the
- *    FP32 evaluation forks its far field onto a handle-owned high-priority stream and joins
- *    it back before its last kernel, so on cfg.stream the call still follows earlier work
- *    and precedes later work.
+ *    reported by the next vfmm_sync().  vfmm_build_tree synchronises the stream once, after
+ *    the key and scatter kernels (the largest leaf sizes the per-leaf sort; non-finite
+ *    positions are reported there); the per-leaf sort runs on after it returns.  With
+ *    concurrent_far the FP32 evaluation forks its far field onto a handle-owned
+ *    high-priority stream and joins it back before its last kernel, so on cfg.stream the
+ *    call still follows earlier work and precedes later work.
  *  - Handles are not thread-safe; use one handle per host thread.
  */
 #ifndef VFMM_H

@@ -626,7 +626,9 @@ int build_impl(Ctx *c, int64_t n, const void *x, double sigma_hint = 0.0)
         return fail(c, VFMM_ERR_UNSUPPORTED, "a leaf holds more particles than the per-leaf sort capacity (4096); use a deeper tree");
     if ((st = launch_leaf_sort(c, x, ml))) return st;
     cudaEventRecord(c->ev[1], c->stream);
-    if ((st = check_device_error(c))) return st;
+    // no second synchronisation: the leaf sort can only raise the checked build's bounds bit
+    // (the largest leaf was checked above), which vfmm_sync reports like any evaluation error;
+    // the caller can queue the evaluation while the sort runs
     c->built = true;
     return VFMM_OK;
 }
