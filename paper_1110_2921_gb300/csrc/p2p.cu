@@ -495,7 +495,9 @@ __global__ void VFMM_P3_BOUNDS k_p2p_f32(const float4 *__restrict__ xs, const fl
         // near rings smoothed with or without the small-rho series, or singular; beyond them the
         // Gaussian-tail correction for octants closer than rho_cut sigma (mode 3), nothing
         // otherwise (mode 4, the M2L has them)); three ballots give every lane the modes of all
-        // 32 octants, so the warp-uniform loop below reads its inner-loop choice per octant.
+        // 32 octants, so the warp-uniform loop below reads its inner-loop choice per octant.  A
+        // mode-3 octant is then tested against the box of each half of the warp's targets (q = 0,
+        // 1), and two more ballots say which halves its pairs run for.
         const int n1 = hi[1] - lo[1] + 1, n2 = hi[2] - lo[2] + 1;
         const int n_off = (hi[0] - lo[0] + 1) * n1 * n2;
         const int lane = threadIdx.x & 31;
